@@ -1,0 +1,457 @@
+"""FP64 oracle for mixed-precision Deep-NN SP2 (arXiv:2101.06385).
+
+TEST INFRASTRUCTURE ONLY -- never called by the product path.
+
+Each function cites the part of the paper it follows.  Pins (checks against
+something other than this file) live in ``tests/test_oracle_*.py``:
+
+=============================  =================================================
+function                       pinned by
+=============================  =================================================
+gershgorin_bounds              Gershgorin circle theorem: bounds enclose the
+                               generator's exact spectrum; hand-computed 2x2/3x3
+input_layer                    spectrum of S0 = reversed affine image of eps
+                               (closed form from the generator)
+sp2                            closed form Q_occ Q_occ^T; 2x2 analytic
+                               projector; N_occ in {0, N}; invariants D^2 = D,
+                               tr D = N_occ, [D, H] = 0; independent scalar
+                               recurrence on the eigenvalues; Fig. 5 layer count
+f_final                        scalar composition 2x^2 - x^4, (2x - x^2)^2
+jacobi_eigh                    generator's exact eigenvalues / vectors; numpy
+                               spectral properties (orthogonality, residual)
+density_matrix_closed_form     Eq. 6 (definition) + invariants
+fermi_dirac_closed_form        kT -> 0 limit equals the projector; trace
+theorem_constant               closed form (71 + 17 sqrt 17)/32 of the appendix
+split_fp16                     brute-force nearest-FP16 search on small inputs;
+                               exact reconstruction bound
+split_square                   exact FP64 product of FP16-exact operands
+network_forward                scalar polynomial composition on eigenvalues
+network_adjoint                central finite differences of network_forward
+=============================  =================================================
+
+Readings of points the paper leaves open (same list as the design notes):
+
+C1  sigma_0 = 0 (no epsilon bias in the first layer).
+C2  Sign(0) = +1.
+C3  epsilon defaults to 0.
+C4  N_S is recomputed as tr S_n after each layer (equal to the paper's
+    update formula in exact arithmetic).
+C7  f_final is applied to the last computed S_n and its branch is read from
+    sigma_{n-2}; when n < 3 (sigma_{n-2} undefined or 0) the x^2-first order
+    (2S^2 - S^4) is used.
+C11 optional ``tol``: stop as soon as IdErr_n <= tol.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+__all__ = [
+    "gershgorin_bounds",
+    "input_layer",
+    "sigma_choice",
+    "sp2",
+    "SP2Result",
+    "f_final",
+    "jacobi_eigh",
+    "density_matrix_closed_form",
+    "density_matrix_jacobi",
+    "fermi_dirac_closed_form",
+    "theorem_ratio",
+    "theorem_constant",
+    "split_fp16",
+    "split_square",
+    "network_forward",
+    "network_loss",
+    "network_adjoint",
+    "sp2_branch_coefficients",
+    "error_metrics",
+    "sp2_layer_sample",
+]
+
+
+# ---------------------------------------------------------------------------
+# Alg. 1, inputs: spectral bound estimates and the input layer
+# ---------------------------------------------------------------------------
+def gershgorin_bounds(H: np.ndarray) -> Tuple[float, float]:
+    """Spectral bound estimates eps_1 <= spec(H) <= eps_N (Alg. 1 inputs).
+
+    Gershgorin circle theorem: every eigenvalue lies in some disc centred at
+    H_ii with radius R_i = sum_{j != i} |H_ij|, so
+    e_min = min_i (H_ii - R_i) and e_max = max_i (H_ii + R_i).
+    """
+    H = np.asarray(H, dtype=np.float64)
+    d = np.diag(H)
+    R = np.abs(H).sum(axis=1) - np.abs(d)
+    return float(np.min(d - R)), float(np.max(d + R))
+
+
+def input_layer(H: np.ndarray, e_min: float, e_max: float) -> np.ndarray:
+    """S_0 = W_0 X_0 + B_0 with X_0 = H (Alg. 1).
+
+    W_0 = -(eps_N - eps_1)^{-1} I and B_0 = eps_N (eps_N - eps_1)^{-1} I map the
+    spectrum of H into [0, 1] in reverse order (lowest energy -> 1).
+    """
+    H = np.asarray(H, dtype=np.float64)
+    width = e_max - e_min
+    W0 = -1.0 / width
+    B0 = e_max / width
+    return W0 * H + B0 * np.eye(H.shape[0])
+
+
+# ---------------------------------------------------------------------------
+# Alg. 1, the layer loop
+# ---------------------------------------------------------------------------
+def sigma_choice(N_S: float, N_X: float, n_occ: float, sigma_prev: int, eps: float) -> int:
+    """sigma_n = Sign(|2 N_S - N_X - N_occ| - |N_X - N_occ| - sigma_{n-1} eps).
+
+    Alg. 1.  sigma = +1 keeps the square X_n (trace N_X); sigma = -1 takes
+    2 S_{n-1} - X_n (trace 2 N_S - N_X); the sign picks the one whose trace
+    is closer to N_occ.  Sign(0) = +1 (reading C2).
+    """
+    v = abs(2.0 * N_S - N_X - n_occ) - abs(N_X - n_occ) - sigma_prev * eps
+    return 1 if v >= 0.0 else -1
+
+
+@dataclasses.dataclass
+class SP2Result:
+    D: np.ndarray                 # final density matrix f_final(S_n)
+    S_last: np.ndarray            # last layer S_n before refinement
+    sigmas: List[int]             # sigma_1 .. sigma_n
+    iderr: List[float]            # IdErr_1 .. IdErr_n
+    traces: List[float]           # tr S_1 .. tr S_n
+    n_layers: int                 # n (number of squaring layers in the loop)
+    converged_by: str             # "tol" | "iderr<=0" | "4.5-rule" | "max_iter"
+    e_min: float
+    e_max: float
+
+
+def sp2(
+    H: np.ndarray,
+    n_occ: int,
+    tol: float = 0.0,
+    max_iter: int = 100,
+    eps: float = 0.0,
+    bounds: Optional[Tuple[float, float]] = None,
+    refine: bool = True,
+) -> SP2Result:
+    """Deep-NN SP2 (Alg. 1) in FP64, followed by the refinement layer (Eq. 15).
+
+    Per layer n = 1, 2, ...:
+      X_n = f(S_{n-1}) = S_{n-1}^2               activation (Alg. 2 in exact form)
+      N_X = Tr[X_n];  IdErr_n = N_S - N_X         idempotency estimate
+      sigma_n from ``sigma_choice``
+      S_n = W_n X_n + B_n,  W_n = sigma_n I,  B_n = (I - W_n) S_{n-1}
+      N_S = Tr[S_n]                               (reading C4)
+      stop if IdErr_n <= tol (C11), or IdErr_n <= 0, or
+           n > 2 and sigma_{n-1} != sigma_{n-2} and IdErr_n > 4.5 IdErr_{n-2}^2
+           (Sec. "Convergence estimate", appendix theorem), or n == max_iter.
+    Then D = f_final(S_n) (Eq. 15, reading C7).
+    """
+    H = np.asarray(H, dtype=np.float64)
+    N = H.shape[0]
+    if bounds is None:
+        e_min, e_max = gershgorin_bounds(H)
+    else:
+        e_min, e_max = bounds
+    S = input_layer(H, e_min, e_max)
+    N_S = float(np.trace(S))
+    sig_hist = [0]          # sigma_0 = 0 (reading C1)
+    err_hist = [math.nan]   # IdErr_0 undefined
+    traces: List[float] = []
+    n = 0
+    how = "max_iter"
+    while True:
+        n += 1
+        X = S @ S
+        N_X = float(np.trace(X))
+        idErr = N_S - N_X
+        sig = sigma_choice(N_S, N_X, n_occ, sig_hist[n - 1], eps)
+        S = sig * X + (1 - sig) * S
+        N_S = float(np.trace(S))
+        sig_hist.append(sig)
+        err_hist.append(idErr)
+        traces.append(N_S)
+        if idErr <= tol and tol > 0.0:
+            how = "tol"
+            break
+        if idErr <= 0.0:
+            how = "iderr<=0"
+            break
+        if n > 2 and sig_hist[n - 1] != sig_hist[n - 2] and idErr > 4.5 * err_hist[n - 2] ** 2:
+            how = "4.5-rule"
+            break
+        if n >= max_iter:
+            how = "max_iter"
+            break
+    s_nm2 = sig_hist[n - 2] if n - 2 >= 1 else 1
+    D = f_final(S, s_nm2) if refine else S.copy()
+    return SP2Result(D=D, S_last=S, sigmas=sig_hist[1:], iderr=err_hist[1:], traces=traces,
+                     n_layers=n, converged_by=how, e_min=e_min, e_max=e_max)
+
+
+def f_final(S: np.ndarray, sigma_nm2: int) -> np.ndarray:
+    """Refinement layer (Eq. 15).
+
+    sigma_{n-2} = +1:  2 S^2 - S^4      (square, then 2x - x^2)
+    sigma_{n-2} = -1:  (2 S - S^2)^2    (2x - x^2, then square)
+    """
+    S = np.asarray(S, dtype=np.float64)
+    S2 = S @ S
+    if sigma_nm2 >= 0:
+        return 2.0 * S2 - S2 @ S2
+    T = 2.0 * S - S2
+    return T @ T
+
+
+# ---------------------------------------------------------------------------
+# Eqs. 4-6: diagonalisation route
+# ---------------------------------------------------------------------------
+def _round_robin(n_even: int):
+    """Pairings of a round-robin tournament on n_even players: n_even - 1
+    rounds, each a perfect matching; every pair meets exactly once."""
+    players = list(range(n_even))
+    for _ in range(n_even - 1):
+        yield [(players[i], players[n_even - 1 - i]) for i in range(n_even // 2)]
+        players = [players[0], players[-1]] + players[1:-1]
+
+
+def jacobi_eigh(A: np.ndarray, tol: float = 1e-15, max_sweeps: int = 60):
+    """Cyclic Jacobi eigensolver (Eq. 4: Q^T H Q = E), FP64.
+
+    Each sweep visits every (p, q) pair once; the pairs are grouped into
+    disjoint matchings (round-robin order) so that one matching is applied as
+    one orthogonal transform A <- J^T A J.  For each pair the rotation
+    (c, s) = (cos phi, sin phi) zeroes A_pq:
+        theta = (A_qq - A_pp) / (2 A_pq),
+        t = sign(theta) / (|theta| + sqrt(theta^2 + 1)),  c = 1/sqrt(t^2+1), s = t c.
+    Returns (eigenvalues ascending, eigenvectors as columns).
+    """
+    A = np.array(A, dtype=np.float64, copy=True)
+    n = A.shape[0]
+    V = np.eye(n)
+    if n == 1:
+        return np.diag(A).copy(), V
+    n_even = n + (n % 2)
+    rounds = []
+    for pairs in _round_robin(n_even):
+        pr = [(p, q) for (p, q) in pairs if p < n and q < n]
+        if pr:
+            P = np.array([min(p, q) for p, q in pr])
+            Qi = np.array([max(p, q) for p, q in pr])
+            rounds.append((P, Qi))
+    scale = np.linalg.norm(A)
+    if scale == 0.0:
+        return np.zeros(n), V
+    for _ in range(max_sweeps):
+        off = np.linalg.norm(A - np.diag(np.diag(A)))
+        if off <= tol * scale:
+            break
+        for P, Qi in rounds:
+            app = A[P, P]
+            aqq = A[Qi, Qi]
+            apq = A[P, Qi]
+            nz = np.abs(apq) > 1e-300
+            theta = np.where(nz, (aqq - app) / np.where(nz, 2.0 * apq, 1.0), 0.0)
+            sgn = np.where(theta >= 0.0, 1.0, -1.0)
+            t = np.where(nz, sgn / (np.abs(theta) + np.hypot(theta, 1.0)), 0.0)
+            c = 1.0 / np.sqrt(t * t + 1.0)
+            s = t * c
+            # A <- A J  (columns p, q)
+            Ap = A[:, P].copy()
+            Aq = A[:, Qi].copy()
+            A[:, P] = Ap * c - Aq * s
+            A[:, Qi] = Ap * s + Aq * c
+            # A <- J^T A  (rows p, q)
+            Ap = A[P, :].copy()
+            Aq = A[Qi, :].copy()
+            A[P, :] = c[:, None] * Ap - s[:, None] * Aq
+            A[Qi, :] = s[:, None] * Ap + c[:, None] * Aq
+            # V <- V J
+            Vp = V[:, P].copy()
+            Vq = V[:, Qi].copy()
+            V[:, P] = Vp * c - Vq * s
+            V[:, Qi] = Vp * s + Vq * c
+    w = np.diag(A).copy()
+    order = np.argsort(w, kind="stable")
+    return w[order], V[:, order]
+
+
+def density_matrix_closed_form(Q: np.ndarray, n_occ: int, rows=None, cols=None) -> np.ndarray:
+    """D = Q theta(mu I - E) Q^T (Eq. 6) with mu in the HOMO-LUMO gap, i.e.
+    the projector on the n_occ lowest eigenvectors: D = Q_occ Q_occ^T.
+
+    Q's columns must be sorted by ascending eigenvalue.  ``rows`` / ``cols``
+    select a sub-block (the rest is never formed), so single entries of a
+    16384 x 16384 D cost O(n_occ) each.
+    """
+    Qo = Q[:, :n_occ]
+    Qr = Qo if rows is None else Qo[rows]
+    Qc = Qo if cols is None else Qo[cols]
+    return Qr @ Qc.T
+
+
+def density_matrix_jacobi(H: np.ndarray, n_occ: int) -> np.ndarray:
+    """Eqs. 4-6 with a hand-written Jacobi diagonalisation."""
+    _, V = jacobi_eigh(H)
+    return density_matrix_closed_form(V, n_occ)
+
+
+def fermi_dirac_closed_form(Q: np.ndarray, eps: np.ndarray, mu: float, kT: float) -> np.ndarray:
+    """D = Q (exp(beta (E - mu I)) + I)^{-1} Q^T with beta = 1/kT (Eqs. 1, 5)."""
+    x = (np.asarray(eps, dtype=np.float64) - mu) / kT
+    # 1/(1+e^x) written to avoid overflow for large |x|
+    f = np.where(x > 0, np.exp(-np.abs(x)) / (1.0 + np.exp(-np.abs(x))), 1.0 / (1.0 + np.exp(-np.abs(x))))
+    return (Q * f[None, :]) @ Q.T
+
+
+# ---------------------------------------------------------------------------
+# Appendix: the convergence theorem
+# ---------------------------------------------------------------------------
+def theorem_ratio(lam: np.ndarray) -> np.ndarray:
+    """((2l - l^2)^2 - (2l - l^2)^4) / (l - l^2)^2: the one-eigenvalue error
+    ratio of two alternating layers (appendix, proof of the theorem)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    y = 2.0 * lam - lam * lam
+    return (y * y - y ** 4) / (lam - lam * lam) ** 2
+
+
+def theorem_constant(grid: int = 200001) -> float:
+    """max over (0, 1) of ``theorem_ratio``, by a dense grid then golden-section
+    refinement.  The appendix states the maximum in closed form."""
+    lam = np.linspace(0.0, 1.0, grid)[1:-1]
+    r = theorem_ratio(lam)
+    k = int(np.argmax(r))
+    a, b = lam[max(k - 1, 0)], lam[min(k + 1, len(lam) - 1)]
+    g = (math.sqrt(5.0) - 1.0) / 2.0
+    for _ in range(200):
+        c = b - g * (b - a)
+        d = a + g * (b - a)
+        if theorem_ratio(np.array([c]))[0] > theorem_ratio(np.array([d]))[0]:
+            b = d
+        else:
+            a = c
+    return float(theorem_ratio(np.array([(a + b) / 2.0]))[0])
+
+
+# ---------------------------------------------------------------------------
+# Eqs. 12-14 / Alg. 2: the split representation (FP64 model of its arithmetic)
+# ---------------------------------------------------------------------------
+def split_fp16(X: np.ndarray, lo_scale_exp: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+    """X^(0) = FP16[X], X^(1) = FP16[(X - X^(0)) * 2^s] (Eq. 12).
+
+    X is taken as FP32 (the stored iterate).  FP16[.] rounds to nearest, ties
+    to even (reading C6); s = ``lo_scale_exp`` scales the low part so that it
+    stays out of the FP16 subnormal range (s = 0 is the paper's literal form).
+    The difference X - X^(0) is exact in FP32.
+    """
+    X32 = np.asarray(X, dtype=np.float32)
+    hi = X32.astype(np.float16)
+    r = (X32 - hi.astype(np.float32)).astype(np.float64) * (2.0 ** lo_scale_exp)
+    lo = r.astype(np.float16)
+    return hi, lo
+
+
+def split_square(hi: np.ndarray, lo: np.ndarray, lo_scale_exp: int = 0, plain: bool = False) -> np.ndarray:
+    """X^2 ~ X0 X0 + X0 X1 + (X0 X1)^T (Eq. 14 / Alg. 2) evaluated in FP64.
+
+    With a scaled low part (X1 stored as 2^s X1) the cross terms carry 2^-s.
+    ``plain`` drops the cross terms (single-FP16 variant).  All operands are
+    exactly representable, so this is the exact value the tensor cores
+    approximate with FP32 accumulation.
+    """
+    h = hi.astype(np.float64)
+    P = h @ h
+    if not plain:
+        B = (h @ lo.astype(np.float64)) * (2.0 ** -lo_scale_exp)
+        P = P + B + B.T
+    return P
+
+
+# ---------------------------------------------------------------------------
+# Eq. 16 in matrix form: the differentiable network X_{n+1} = a X^2 + b X + c I
+# ---------------------------------------------------------------------------
+def network_forward(X0: np.ndarray, coef: np.ndarray, keep: bool = False):
+    """X_{n+1} = a_n X_n^2 + b_n X_n + c_n I for n = 0..L-1 (Eq. 16 applied to
+    a matrix: the polynomial acts on the eigenvalues).  ``coef`` is [L, 3]
+    (a_n, b_n, c_n).  X0 may be batched [B, N, N].  Returns X_L (and the list
+    of all X_n when ``keep``)."""
+    X = np.asarray(X0, dtype=np.float64)
+    coef = np.asarray(coef, dtype=np.float64)
+    N = X.shape[-1]
+    I = np.eye(N)
+    xs = [X]
+    for a, b, c in coef:
+        X = a * (X @ X) + b * X + c * I
+        xs.append(X)
+    return (X, xs) if keep else X
+
+
+def network_loss(XL: np.ndarray, target: np.ndarray) -> float:
+    """L = (1/B) sum_b ||X_L^(b) - D^(b)||_F^2 (squared Frobenius distance)."""
+    XL = np.asarray(XL, dtype=np.float64)
+    B = XL.shape[0] if XL.ndim == 3 else 1
+    return float(np.sum((XL - target) ** 2) / B)
+
+
+def network_adjoint(X0: np.ndarray, coef: np.ndarray, G_L: np.ndarray):
+    """Reverse-mode derivative of ``network_forward``.
+
+    With G_{n+1} = dL/dX_{n+1} and symmetric X_n:
+      G_n   = a_n (X_n G_{n+1} + G_{n+1} X_n) + b_n G_{n+1}
+      da_n  = <G_{n+1}, X_n^2>,  db_n = <G_{n+1}, X_n>,  dc_n = tr G_{n+1}
+    (sums over the batch).  Returns (dcoef [L,3], G_0).
+    """
+    coef = np.asarray(coef, dtype=np.float64)
+    _, xs = network_forward(X0, coef, keep=True)
+    G = np.asarray(G_L, dtype=np.float64)
+    L = coef.shape[0]
+    dcoef = np.zeros((L, 3))
+    for n in range(L - 1, -1, -1):
+        a, b, _ = coef[n]
+        X = xs[n]
+        X2 = X @ X
+        dcoef[n, 0] = np.sum(G * X2)
+        dcoef[n, 1] = np.sum(G * X)
+        dcoef[n, 2] = float(np.sum(np.trace(G, axis1=-2, axis2=-1)))
+        G = a * (X @ G + G @ X) + b * G
+    return dcoef, G
+
+
+def sp2_branch_coefficients(sigmas: Sequence[int], L: int) -> np.ndarray:
+    """Network coefficients equal to an SP2 branch sequence: sigma = +1 gives
+    x^2 -> (a, b, c) = (1, 0, 0); sigma = -1 gives 2x - x^2 -> (-1, 2, 0)."""
+    coef = np.zeros((L, 3))
+    for n in range(L):
+        s = sigmas[n] if n < len(sigmas) else (1 if n % 2 == 0 else -1)
+        coef[n] = (1.0, 0.0, 0.0) if s > 0 else (-1.0, 2.0, 0.0)
+    return coef
+
+
+# ---------------------------------------------------------------------------
+# Error metrics and a bounded timing sample
+# ---------------------------------------------------------------------------
+def error_metrics(D: np.ndarray, D_ref: np.ndarray, n_occ: Optional[int] = None) -> dict:
+    D = np.asarray(D, dtype=np.float64)
+    D_ref = np.asarray(D_ref, dtype=np.float64)
+    diff = D - D_ref
+    out = {
+        "max_abs": float(np.max(np.abs(diff))) if diff.size else 0.0,
+        "rel_frobenius": float(np.linalg.norm(diff) / max(np.linalg.norm(D_ref), 1e-300)),
+    }
+    if n_occ is not None:
+        out["trace_err"] = float(abs(np.trace(D) - n_occ))
+    return out
+
+
+def sp2_layer_sample(S: np.ndarray, rows: int) -> float:
+    """One SP2 layer restricted to the first ``rows`` rows of the product
+    (activation + update + trace contribution): the bounded CPU workload used
+    for timing the oracle.  Returns a checksum so the work is not elided."""
+    Sr = S[:rows]
+    X = Sr @ S
+    Snew = 2.0 * Sr - X
+    return float(np.trace(Snew[:, :rows]))
