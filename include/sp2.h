@@ -1,0 +1,196 @@
+/*
+ * sp2.h -- C ABI of the GB300 (sm_103a) SP2 density-matrix library.
+ *
+ * Method: mixed-precision Deep-NN SP2 recursive Fermi-operator expansion of
+ * Finkelstein et al., "Mixed Precision Fermi-Operator Expansion on Tensor
+ * Cores From a Machine Learning Perspective" (arXiv:2101.06385):
+ *   Alg. 1  (layer loop, branch choice, parameter-free convergence),
+ *   Alg. 2 / Eqs. 12-14 (split FP16 hi/lo squaring with FP32 accumulation),
+ *   Eq. 15  (refinement layer f_final),
+ *   Eq. 16  (generalised second-order layer, used by the network entry points).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are dense, real, symmetric, row-major float32 with leading
+ *   dimension N (no padding).  Symmetry is assumed, not checked.
+ * - Unless stated otherwise every matrix pointer is a DEVICE pointer on the
+ *   device selected in sp2_init, owned by the caller; the library neither
+ *   frees nor retains it after the call returns.  Host pointers are marked.
+ * - All device work is enqueued on the library stream (sp2_config.stream, or
+ *   the one set with sp2_set_stream).  A call with a non-NULL stats pointer
+ *   synchronises that stream before returning; with stats == NULL the call
+ *   only enqueues.
+ * - Return value: SP2_OK (0), SP2_NOT_CONVERGED (> 0, outputs still written)
+ *   or a negative error.  On SP2_ERR_INVALID_ARG nothing is enqueued and the
+ *   outputs are untouched.  Errors found on the device (non-finite or
+ *   degenerate spectral bounds, device wait time-outs) are reported through
+ *   the status of a synchronising call; outputs are then unspecified.
+ * - No C++ exception crosses this interface.  sp2_last_error() returns a
+ *   thread-local description of the last failure.
+ * - Not re-entrant: one thread at a time per process (the workspace is
+ *   shared).
+ */
+#ifndef SP2_H
+#define SP2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SP2_MAX_LAYERS 128 /* max_iter <= SP2_MAX_LAYERS - 3 */
+
+typedef enum {
+  SP2_OK = 0,
+  SP2_NOT_CONVERGED = 1,
+  SP2_ERR_INVALID_ARG = -1,
+  SP2_ERR_NOT_INITIALIZED = -2,
+  SP2_ERR_DEGENERATE_SPECTRUM = -3, /* e_max - e_min <= 0 with 0 < N_occ < N */
+  SP2_ERR_NONFINITE = -4,           /* non-finite spectral bounds (NaN/Inf in H) */
+  SP2_ERR_CUDA = -5,
+  SP2_ERR_OOM = -6,
+  SP2_ERR_DEVICE_TIMEOUT = -7,      /* a bounded device wait ran out */
+  SP2_ERR_UNSUPPORTED = -8
+} sp2_status;
+
+typedef enum {
+  SP2_PREC_SPLIT_FP16 = 0, /* Alg. 2: X ~ hi + lo, X^2 ~ hi hi + hi lo + lo hi, FP32 accumulate (tcgen05) */
+  SP2_PREC_FP16 = 1,       /* single FP16 product hi hi, FP32 accumulate (tcgen05) */
+  SP2_PREC_FP32 = 2        /* FP32 FFMA on the CUDA cores: the paper's "GPU-only" comparator */
+} sp2_precision;
+
+typedef enum {
+  SP2_STOP_NONE = 0,
+  SP2_STOP_TOL = 1,      /* IdErr_n <= tol */
+  SP2_STOP_IDERR = 2,    /* IdErr_n <= 0 (Alg. 1) */
+  SP2_STOP_RULE45 = 3,   /* IdErr_n > 4.5 IdErr_{n-2}^2 after a sign change (Alg. 1, appendix) */
+  SP2_STOP_MAXITER = 4   /* n == max_iter: returns SP2_NOT_CONVERGED */
+} sp2_stop_reason;
+
+typedef struct {
+  int device;             /* CUDA device ordinal */
+  void* stream;           /* cudaStream_t; NULL selects the legacy default stream */
+  int precision;          /* sp2_precision */
+  int lo_scale_exp;       /* s: the low FP16 part stores 2^s (X - hi); default 11, range 0..14 */
+  int shift_identity;     /* 1 (default): iterate S = alpha I + Y with FP64 alpha, square only Y */
+  double eps_bias;        /* epsilon of the branch rule (Alg. 1); default 0 */
+} sp2_config;
+
+typedef struct {
+  int iterations;                 /* n: squaring layers of the loop (refinement not counted) */
+  int converged_by;               /* sp2_stop_reason */
+  int status_device;              /* sp2_status recorded on the device */
+  int n_occ;
+  double e_min, e_max;            /* Gershgorin bounds used for the input layer */
+  double idemp_err;               /* IdErr_n of the last loop layer (Tr[S - S^2]) */
+  double trace;                   /* tr D after refinement */
+  double alpha;                   /* identity shift of the last iterate (0 without shift) */
+  double time_ms;                 /* device time of the whole call (CUDA events) */
+  double flops_alg;               /* algorithmic FLOPs: layers x 3N^3 (split), N^3 (fp16/fp32) */
+  int8_t sigma[SP2_MAX_LAYERS];   /* sigma[k] = sigma_{k+1} in {+1,-1}; 0 past the end */
+  double iderr[SP2_MAX_LAYERS];   /* iderr[k] = IdErr_{k+1} */
+} sp2_stats;
+
+/* Library set-up.  cfg == NULL selects the defaults {device 0, NULL stream,
+ * SPLIT_FP16, s = 11, shift on, eps 0}.  Calling again re-applies a config
+ * (the workspace is kept).  Errors: INVALID_ARG (bad field), CUDA. */
+sp2_status sp2_init(const sp2_config* cfg);
+
+/* Frees the workspace.  Safe to call when not initialised. */
+sp2_status sp2_finalize(void);
+
+/* Selects the stream for subsequent calls (cudaStream_t, NULL = default). */
+sp2_status sp2_set_stream(void* stream);
+
+/* Selects the precision for subsequent calls (sp2_precision). */
+sp2_status sp2_set_precision(int precision);
+
+/* Thread-local text of the last error ("" if none).  Never NULL. */
+const char* sp2_last_error(void);
+
+/*
+ * Zero-temperature density matrix D = theta(mu I - H) with Tr D = N_occ by
+ * Deep-NN SP2 (Alg. 1) with the refinement layer f_final (Eq. 15).
+ *
+ *   H        [N, N] device, input Hamiltonian (orthonormal basis, Sec. 2).
+ *   N        matrix size, 1 <= N <= 65536.
+ *   N_occ    number of occupied states, 0 <= N_occ <= N.
+ *   tol      stop once IdErr_n <= tol (0: only the paper's parameter-free rule).
+ *   max_iter 1 <= max_iter <= SP2_MAX_LAYERS - 3.
+ *   D_out    [N, N] device output; also used as the iterate's storage during
+ *            the call.  Must not alias H.
+ *   stats    host pointer or NULL (see conventions).
+ * Spectral bounds: Gershgorin discs (Alg. 1 "spectral bound estimates").
+ */
+sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int max_iter,
+                              float* D_out, sp2_stats* stats);
+
+/*
+ * Many independent SP2 problems of uneven size in grouped launches (the
+ * batching remark of Sec. 4).  H, N, N_occ, D_out are HOST arrays of length
+ * batch; H[i] and D_out[i] are device pointers to [N[i], N[i]] matrices.
+ * Each instance follows its own branch sequence and convergence.  Sizes
+ * 1 <= N[i] <= 4096, batch <= 4096.  stats: host array [batch] or NULL.
+ * Returns SP2_NOT_CONVERGED if any instance hit max_iter.
+ */
+sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const int* N_occ, int batch,
+                                      double tol, int max_iter, float* const* D_out, sp2_stats* stats);
+
+/*
+ * Differentiable network (Eq. 16 in matrix form), batched over B instances:
+ *   X_0 = (e_max I - H)/(e_max - e_min)    (Gershgorin bounds per instance, Alg. 1 input layer)
+ *   X_{n+1} = a_n X_n^2 + b_n X_n + c_n I,  n = 0 .. L-1,
+ * with X^2 computed by the split-FP16 tensor-core squaring.
+ *   H      [B, N, N] device.        coef  [L, 3] HOST float (a_n, b_n, c_n).
+ *   X_out  [B, N, N] device, X_L.
+ *   ckpt   [(L / ckpt_every) + 1, B, N, N] device or NULL: X_{k ckpt_every}
+ *          for k = 0 .. L / ckpt_every, in that order.
+ *   bounds [B, 2] device double or NULL: receives (e_min, e_max) per instance.
+ * 1 <= L <= 256, 1 <= ckpt_every <= L, B * N * N < 2^31, N <= 8192.
+ */
+sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float* coef, int ckpt_every,
+                               float* X_out, float* ckpt, double* bounds);
+
+/*
+ * Adjoint of sp2_network_forward (reverse mode, layer checkpointing).
+ *   ckpt   the checkpoints written by sp2_network_forward with the same
+ *          H, B, N, L, coef, ckpt_every.
+ *   G_out  [B, N, N] device, dLoss/dX_L (symmetric).
+ *   dcoef  [L, 3] HOST double output: (dL/da_n, dL/db_n, dL/dc_n) summed over the batch.
+ *   G_in   [B, N, N] device output dLoss/dX_0, or NULL.
+ * Per layer, with G = G_{n+1}:  G_n = a_n (X_n G + G X_n) + b_n G,
+ *   dL/da_n = <G, X_n^2>, dL/db_n = <G, X_n>, dL/dc_n = tr G.
+ */
+sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float* coef, int ckpt_every,
+                                const float* ckpt, const float* G_out, double* dcoef, float* G_in);
+
+/* ---- single steps of the path, exposed for testing and composition ---- */
+
+/* Gershgorin spectral bounds (Alg. 1 inputs): bounds_out (HOST double[2]) =
+ * { min_i H_ii - R_i, max_i H_ii + R_i }, R_i = sum_{j != i} |H_ij|,
+ * accumulated in FP64.  Synchronises.  1 <= N <= 65536. */
+sp2_status sp2_gershgorin(const float* H, int N, double* bounds_out);
+
+/* Split of an FP32 matrix into FP16 parts (Eq. 12), round-to-nearest-even:
+ * hi = FP16[X], lo = FP16[2^s (X - hi)].  X [N, N] device float; hi, lo
+ * [N, N] device uint16 (IEEE binary16 bit patterns).  0 <= s <= 14. */
+sp2_status sp2_split(const float* X, int N, int lo_scale_exp, uint16_t* hi, uint16_t* lo);
+
+/* One generalised layer (Eq. 16) through the selected precision's squaring
+ * kernel: X_out = a X^2 + b X + c I for a batch of B matrices [B, N, N].
+ * traces_out: HOST double[2 B] or NULL -> (tr X_out, ||X_out||_F^2) per
+ * matrix (synchronises when non-NULL).  X_out must not alias X. */
+sp2_status sp2_layer(const float* X, int B, int N, float a, float b, float c, float* X_out,
+                     double* traces_out);
+
+/* Observable alpha = Tr[D A] (Alg. 1, last line; A = H gives the band
+ * energy).  D, A [N, N] device; out: HOST double.  Synchronises. */
+sp2_status sp2_observable(const float* D, const float* A, int N, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SP2_H */

@@ -1,0 +1,670 @@
+// C ABI of libsp2.so: argument checks, workspace, launch sequences.
+//
+// A call of sp2_density_matrix enqueues, on the library stream:
+//   K1 Gershgorin bounds -> K2 input layer + split + first control step ->
+//   (max_iter + 2) squaring launches.  Each squaring launch reads the layer
+//   coefficients that the previous launch's control step left on the device
+//   and does nothing once the solve has finished, so no host round trip is
+//   needed inside the loop.  The two launches after the loop's last layer
+//   are the refinement of Eq. 15; the last one writes D_out.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sp2.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace sp2;
+
+namespace {
+
+thread_local std::string t_err;
+
+void set_err(const char* fmt, ...) __attribute__((format(printf, 1, 2)));
+void set_err(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+}
+
+#define CK(expr)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (expr);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      set_err("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? SP2_ERR_OOM : SP2_ERR_CUDA;            \
+    }                                                                                 \
+  } while (0)
+
+#define CKS(expr)                   \
+  do {                              \
+    sp2_status s_ = (expr);         \
+    if (s_ != SP2_OK) return s_;    \
+  } while (0)
+
+enum BufId {
+  B_HI0, B_LO0, B_HI1, B_LO1, B_Y0, B_Y1, B_CTL, B_TILES, B_TOFF, B_TCNT, B_TPART, B_IDONE,
+  B_PART, B_TICKET, B_ERR, B_DPTR, B_NS, B_HS, B_TRACES, B_PARAMS, B_BOUNDS, B_COUNT
+};
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct State {
+  bool init = false;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int precision = SP2_PREC_SPLIT_FP16;
+  int lo_scale_exp = 11;
+  int shift = 1;
+  double eps = 0.0;
+  int num_sms = 148;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  Buf buf[B_COUNT];
+  // pinned staging for small host<->device transfers
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t stage_done = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // cached tile list
+  int tiles_key_N = -1, tiles_key_B = -1, tiles_key_kind = -1;
+};
+
+State g;
+
+sp2_status ws(BufId id, size_t bytes, void** out, bool zero = false) {
+  Buf& b = g.buf[id];
+  if (bytes == 0) bytes = 16;
+  if (b.bytes < bytes) {
+    if (b.p) {
+      CK(cudaStreamSynchronize(g.stream));
+      CK(cudaFree(b.p));
+      b.p = nullptr;
+      b.bytes = 0;
+    }
+    CK(cudaMalloc(&b.p, bytes));
+    b.bytes = bytes;
+    if (id == B_TILES || id == B_TOFF || id == B_TCNT) g.tiles_key_N = -1;
+    zero = true;
+  }
+  if (zero) CK(cudaMemsetAsync(b.p, 0, b.bytes, g.stream));
+  *out = b.p;
+  return SP2_OK;
+}
+
+sp2_status staging(size_t bytes, void** out) {
+  if (g.stage_done) CK(cudaEventSynchronize(g.stage_done));
+  if (g.stage_bytes < bytes) {
+    if (g.stage) CK(cudaFreeHost(g.stage));
+    g.stage = nullptr;
+    CK(cudaMallocHost(&g.stage, bytes));
+    g.stage_bytes = bytes;
+  }
+  *out = g.stage;
+  return SP2_OK;
+}
+
+sp2_status require_init() {
+  if (!g.init) {
+    set_err("sp2_init has not been called");
+    return SP2_ERR_NOT_INITIALIZED;
+  }
+  CK(cudaSetDevice(g.device));
+  return SP2_OK;
+}
+
+inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+// Upper-triangle tile list in grouped order: groups of 8 x 8 block tiles
+// are visited upper-triangle first, block tiles row-major inside a group, so
+// that the CTAs running at the same time share row panels in L2.
+void build_tiles(int N, int B, int tile, bool halves, std::vector<uint32_t>& out, int& per_instance) {
+  const int T = (N + tile - 1) / tile;
+  const int G = 8;
+  std::vector<uint32_t> one;
+  for (int gi = 0; gi < T; gi += G)
+    for (int gj = gi; gj < T; gj += G)
+      for (int I = gi; I < std::min(gi + G, T); ++I)
+        for (int J = std::max(I, gj); J < std::min(gj + G, T); ++J) {
+          if (halves) {
+            one.push_back(pack_tile(0, I, J, 0));
+            if (I * tile + tile / 2 < N) one.push_back(pack_tile(0, I, J, 1));
+          } else {
+            one.push_back(pack_tile(0, I, J, 0));
+          }
+        }
+  per_instance = (int)one.size();
+  out.clear();
+  out.reserve((size_t)per_instance * B);
+  for (int b = 0; b < B; ++b)
+    for (uint32_t t : one) out.push_back(t | ((uint32_t)b << 20));
+}
+
+bool tc_precision(int p) { return p == SP2_PREC_SPLIT_FP16 || p == SP2_PREC_FP16; }
+
+// Uploads a uniform-size tile list (B instances of size N).
+sp2_status upload_tiles(int N, int B, bool tc, int* ntiles_out) {
+  std::vector<uint32_t> tiles;
+  int per = 0;
+  build_tiles(N, B, tc ? kTcBN : kSimtB, tc, tiles, per);
+  const int nt = (int)tiles.size();
+  void *dt, *doff, *dcnt, *dpart, *ddone;
+  CKS(ws(B_TILES, nt * sizeof(uint32_t), &dt));
+  CKS(ws(B_TOFF, B * sizeof(int), &doff));
+  CKS(ws(B_TCNT, B * sizeof(int), &dcnt));
+  CKS(ws(B_TPART, nt * sizeof(double2), &dpart));
+  CKS(ws(B_IDONE, B * sizeof(unsigned), &ddone, true));
+  const int kind = tc ? 1 : 0;
+  if (!(g.tiles_key_N == N && g.tiles_key_B == B && g.tiles_key_kind == kind)) {
+    size_t bytes = nt * sizeof(uint32_t) + 2 * B * sizeof(int);
+    void* h;
+    CKS(staging(bytes, &h));
+    uint8_t* hp = (uint8_t*)h;
+    memcpy(hp, tiles.data(), nt * sizeof(uint32_t));
+    int* off = (int*)(hp + nt * sizeof(uint32_t));
+    int* cnt = off + B;
+    for (int b = 0; b < B; ++b) {
+      off[b] = b * per;
+      cnt[b] = per;
+    }
+    CK(cudaMemcpyAsync(dt, hp, nt * sizeof(uint32_t), cudaMemcpyHostToDevice, g.stream));
+    CK(cudaMemcpyAsync(doff, off, B * sizeof(int), cudaMemcpyHostToDevice, g.stream));
+    CK(cudaMemcpyAsync(dcnt, cnt, B * sizeof(int), cudaMemcpyHostToDevice, g.stream));
+    CK(cudaEventRecord(g.stage_done, g.stream));
+    g.tiles_key_N = N;
+    g.tiles_key_B = B;
+    g.tiles_key_kind = kind;
+  }
+  *ntiles_out = nt;
+  return SP2_OK;
+}
+
+}  // namespace
+
+namespace sp2 {
+bool make_tmap_f16(CUtensorMap* out, const void* base, int cols, int rows, int batch, long long ld, long long slot,
+                   int box_k, int box_rows) {
+  if (!g.encode) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)slot * 2};
+  cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g.encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+}  // namespace sp2
+
+namespace {
+
+// Tensor maps {hiA, loA, hiB, loB} over split buffers (hi, lo) of B
+// instances with N x N used entries, row stride ld_h, slot stride slot_h.
+sp2_status tmaps_for(const void* hi, const void* lo, int N, int B, long long ld_h, long long slot_h, CUtensorMap* m) {
+  const void* lo_ = lo ? lo : hi;
+  bool ok = make_tmap_f16(&m[0], hi, N, N, B, ld_h, slot_h, 32, kTcBM) &&
+            make_tmap_f16(&m[1], lo_, N, N, B, ld_h, slot_h, 32, kTcBM) &&
+            make_tmap_f16(&m[2], hi, N, N, B, ld_h, slot_h, 32, kTcBN) &&
+            make_tmap_f16(&m[3], lo_, N, N, B, ld_h, slot_h, 32, kTcBN);
+  if (!ok) {
+    set_err("cuTensorMapEncodeTiled failed (N=%d, ld=%lld)", N, ld_h);
+    return SP2_ERR_CUDA;
+  }
+  return SP2_OK;
+}
+
+void init_ctl(Ctl* c, int N, int n_occ, double tol, int max_iter) {
+  memset(c, 0, sizeof(Ctl));
+  c->N = N;
+  c->n_occ = n_occ;
+  c->max_iter = max_iter;
+  c->shift = g.shift;
+  c->tol = tol;
+  c->eps = g.eps;
+  c->phase = PHASE_LOOP;
+  c->status = SP2_OK;
+}
+
+void fill_stats(const Ctl& c, sp2_stats* s, double ms, int precision) {
+  memset(s, 0, sizeof(*s));
+  s->iterations = c.n;
+  s->converged_by = c.converged_by;
+  s->status_device = c.status;
+  s->n_occ = c.n_occ;
+  s->e_min = c.e_min;
+  s->e_max = c.e_max;
+  s->idemp_err = (c.n >= 1 && c.n <= kMaxL) ? c.iderr[c.n] : 0.0;
+  s->trace = c.trace_final;
+  s->alpha = c.alpha;
+  s->time_ms = ms;
+  const double N = (double)c.N;
+  const double per = (precision == SP2_PREC_SPLIT_FP16 ? 3.0 : 1.0) * N * N * N;
+  s->flops_alg = (c.phase == PHASE_DONE ? (c.n + 2) : c.n) * per;
+  for (int k = 0; k < kMaxL; ++k) {
+    s->sigma[k] = (k + 1 <= c.n) ? (int8_t)c.sigma[k + 1] : 0;
+    s->iderr[k] = (k + 1 <= c.n) ? c.iderr[k + 1] : 0.0;
+  }
+}
+
+sp2_status status_of(const Ctl& c, int dev_err) {
+  if (dev_err != 0) {
+    set_err("a bounded device wait timed out");
+    return SP2_ERR_DEVICE_TIMEOUT;
+  }
+  if (c.status < 0) {
+    set_err(c.status == SP2_ERR_NONFINITE ? "non-finite spectral bounds (NaN or Inf in H)"
+                                          : "degenerate spectrum: e_max - e_min <= 0 with 0 < N_occ < N");
+    return (sp2_status)c.status;
+  }
+  if (c.phase != PHASE_DONE) {
+    set_err("solve did not finish (phase %d)", c.phase);
+    return SP2_ERR_CUDA;
+  }
+  if (c.converged_by == SP2_STOP_MAXITER) return SP2_NOT_CONVERGED;
+  return SP2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sp2_status sp2_init(const sp2_config* cfg) {
+  t_err.clear();
+  sp2_config c;
+  c.device = 0;
+  c.stream = nullptr;
+  c.precision = SP2_PREC_SPLIT_FP16;
+  c.lo_scale_exp = 11;
+  c.shift_identity = 1;
+  c.eps_bias = 0.0;
+  if (cfg) c = *cfg;
+  if (c.precision < 0 || c.precision > 2 || c.lo_scale_exp < 0 || c.lo_scale_exp > 14 || !std::isfinite(c.eps_bias) ||
+      c.device < 0) {
+    set_err("invalid sp2_config field");
+    return SP2_ERR_INVALID_ARG;
+  }
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (c.device >= ndev) {
+    set_err("device %d not present (%d devices)", c.device, ndev);
+    return SP2_ERR_INVALID_ARG;
+  }
+  if (g.init && g.device != c.device) sp2_finalize();
+  CK(cudaSetDevice(c.device));
+  int major = 0, minor = 0;
+  CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c.device));
+  CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, c.device));
+  if (major != 10) {
+    set_err("libsp2 is built for sm_103a (compute capability 10.x); device has %d.%d", major, minor);
+    return SP2_ERR_UNSUPPORTED;
+  }
+  CK(cudaDeviceGetAttribute(&g.num_sms, cudaDevAttrMultiProcessorCount, c.device));
+  if (!g.encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (!fn || q != cudaDriverEntryPointSuccess) {
+      set_err("cuTensorMapEncodeTiled not available from the driver");
+      return SP2_ERR_UNSUPPORTED;
+    }
+    g.encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  if (!g.stage_done) {
+    CK(cudaEventCreateWithFlags(&g.stage_done, cudaEventDisableTiming));
+    CK(cudaEventCreate(&g.ev0));
+    CK(cudaEventCreate(&g.ev1));
+  }
+  g.device = c.device;
+  g.stream = (cudaStream_t)c.stream;
+  g.precision = c.precision;
+  g.lo_scale_exp = c.lo_scale_exp;
+  g.shift = c.shift_identity ? 1 : 0;
+  g.eps = c.eps_bias;
+  g.init = true;
+  return SP2_OK;
+}
+
+sp2_status sp2_finalize(void) {
+  if (!g.init) return SP2_OK;
+  cudaSetDevice(g.device);
+  cudaStreamSynchronize(g.stream);
+  for (int i = 0; i < B_COUNT; ++i) {
+    if (g.buf[i].p) cudaFree(g.buf[i].p);
+    g.buf[i] = Buf();
+  }
+  if (g.stage) cudaFreeHost(g.stage);
+  g.stage = nullptr;
+  g.stage_bytes = 0;
+  if (g.stage_done) cudaEventDestroy(g.stage_done);
+  if (g.ev0) cudaEventDestroy(g.ev0);
+  if (g.ev1) cudaEventDestroy(g.ev1);
+  g.stage_done = g.ev0 = g.ev1 = nullptr;
+  g.tiles_key_N = -1;
+  g.init = false;
+  return SP2_OK;
+}
+
+sp2_status sp2_set_stream(void* stream) {
+  CKS(require_init());
+  g.stream = (cudaStream_t)stream;
+  return SP2_OK;
+}
+
+sp2_status sp2_set_precision(int precision) {
+  CKS(require_init());
+  if (precision < 0 || precision > 2) {
+    set_err("precision must be 0 (split), 1 (fp16) or 2 (fp32)");
+    return SP2_ERR_INVALID_ARG;
+  }
+  g.precision = precision;
+  return SP2_OK;
+}
+
+const char* sp2_last_error(void) { return t_err.c_str(); }
+
+sp2_status sp2_gershgorin(const float* H, int N, double* bounds_out) {
+  t_err.clear();
+  CKS(require_init());
+  if (!H || !bounds_out || N < 1 || N > 65536) {
+    set_err("sp2_gershgorin: invalid argument");
+    return SP2_ERR_INVALID_ARG;
+  }
+  const int grid = (int)std::min<long long>((N + 7) / 8, 4LL * g.num_sms);
+  void *part, *tick, *bnd;
+  CKS(ws(B_PART, grid * sizeof(double2), &part));
+  CKS(ws(B_TICKET, 64 * sizeof(unsigned), &tick, true));
+  CKS(ws(B_BOUNDS, 2 * sizeof(double), &bnd));
+  CK(launch_gershgorin(H, N, N, (long long)N * N, 1, (double2*)part, (unsigned*)tick, nullptr, (double*)bnd, grid,
+                       g.stream));
+  CK(cudaMemcpyAsync(bounds_out, bnd, 2 * sizeof(double), cudaMemcpyDeviceToHost, g.stream));
+  CK(cudaStreamSynchronize(g.stream));
+  return SP2_OK;
+}
+
+sp2_status sp2_split(const float* X, int N, int lo_scale_exp, uint16_t* hi, uint16_t* lo) {
+  t_err.clear();
+  CKS(require_init());
+  if (!X || !hi || !lo || N < 1 || N > 65536 || lo_scale_exp < 0 || lo_scale_exp > 14) {
+    set_err("sp2_split: invalid argument");
+    return SP2_ERR_INVALID_ARG;
+  }
+  const long long n = (long long)N * N;
+  const int grid = (int)std::min<long long>((n + 255) / 256, 8LL * g.num_sms);
+  CK(launch_split(X, n, std::ldexp(1.0f, lo_scale_exp), (__half*)hi, (__half*)lo, grid, g.stream));
+  return SP2_OK;
+}
+
+sp2_status sp2_observable(const float* D, const float* A, int N, double* out) {
+  t_err.clear();
+  CKS(require_init());
+  if (!D || !A || !out || N < 1 || N > 65536) {
+    set_err("sp2_observable: invalid argument");
+    return SP2_ERR_INVALID_ARG;
+  }
+  const long long n = (long long)N * N;
+  const int grid = (int)std::min<long long>((n + 1023) / 1024, 4LL * g.num_sms);
+  void* part;
+  CKS(ws(B_PART, grid * sizeof(double2), &part));
+  CK(launch_observable(D, A, n, (double*)part, grid, g.stream));
+  void* h;
+  CKS(staging(grid * sizeof(double), &h));
+  CK(cudaMemcpyAsync(h, part, grid * sizeof(double), cudaMemcpyDeviceToHost, g.stream));
+  CK(cudaStreamSynchronize(g.stream));
+  double s = 0.0;
+  for (int i = 0; i < grid; ++i) s += ((double*)h)[i];
+  *out = s;
+  return SP2_OK;
+}
+
+sp2_status sp2_layer(const float* X, int B, int N, float a, float b, float c, float* X_out, double* traces_out) {
+  t_err.clear();
+  CKS(require_init());
+  if (!X || !X_out || X == X_out || B < 1 || N < 1 || N > 65536 || (long long)B * N > (1LL << 31) || B > 4096 ||
+      !std::isfinite(a) || !std::isfinite(b) || !std::isfinite(c)) {
+    set_err("sp2_layer: invalid argument");
+    return SP2_ERR_INVALID_ARG;
+  }
+  const bool tc = tc_precision(g.precision);
+  const bool split = g.precision == SP2_PREC_SPLIT_FP16;
+  int ntiles = 0;
+  CKS(upload_tiles(N, B, tc, &ntiles));
+  void *ns, *params, *traces, *err, *dptr;
+  CKS(ws(B_NS, B * sizeof(int), &ns));
+  CKS(ws(B_PARAMS, sizeof(LayerParams), &params));
+  CKS(ws(B_TRACES, 2 * B * sizeof(double), &traces));
+  CKS(ws(B_ERR, sizeof(int), &err, true));
+  CKS(ws(B_DPTR, B * sizeof(float*), &dptr));
+  void* h;
+  CKS(staging(B * sizeof(int) + sizeof(LayerParams), &h));
+  int* hn = (int*)h;
+  for (int i = 0; i < B; ++i) hn[i] = N;
+  LayerParams* hp = (LayerParams*)(hn + B);
+  memset(hp, 0, sizeof(*hp));
+  hp->ca = b;
+  hp->cb = a;
+  hp->cc = c;
+  hp->active = 1;
+  hp->out_mode = OUT_Y;
+  CK(cudaMemcpyAsync(ns, hn, B * sizeof(int), cudaMemcpyHostToDevice, g.stream));
+  CK(cudaMemcpyAsync(params, hp, sizeof(LayerParams), cudaMemcpyHostToDevice, g.stream));
+  CK(cudaEventRecord(g.stage_done, g.stream));
+
+  SqArgs A;
+  memset(&A, 0, sizeof(A));
+  A.Yin = X;
+  A.Yout = X_out;
+  A.ld_y = N;
+  A.slot_y = (long long)N * N;
+  A.Dptr = (float* const*)dptr;
+  A.Ns = (const int*)ns;
+  A.tiles = (const uint32_t*)g.buf[B_TILES].p;
+  A.ntiles = ntiles;
+  A.tile_off = (const int*)g.buf[B_TOFF].p;
+  A.tile_cnt = (const int*)g.buf[B_TCNT].p;
+  A.ctl = nullptr;
+  A.lp = (const LayerParams*)params;
+  A.lp_per_instance = 0;
+  A.tile_part = (double2*)g.buf[B_TPART].p;
+  A.inst_done = (unsigned*)g.buf[B_IDONE].p;
+  A.traces_out = (double*)traces;
+  A.lo_scale = std::ldexp(1.0f, g.lo_scale_exp);
+  A.lo_unscale = std::ldexp(1.0f, -g.lo_scale_exp);
+  A.err = (int*)err;
+  if (tc) {
+    const long long ld_h = round_up(N, 64), slot_h = ld_h * N;
+    void *hi, *lo = nullptr;
+    CKS(ws(B_HI0, (size_t)slot_h * B * 2, &hi));
+    if (split) CKS(ws(B_LO0, (size_t)slot_h * B * 2, &lo));
+    const int grid = (int)std::min<long long>((long long)N * B, 8LL * g.num_sms);
+    CK(launch_split_pad(X, N, (long long)N * N, N, B, A.lo_scale, (__half*)hi, (__half*)lo, ld_h, slot_h, grid,
+                        g.stream));
+    CUtensorMap m[4];
+    CKS(tmaps_for(hi, lo, N, B, ld_h, slot_h, m));
+    A.hi_out = nullptr;
+    A.lo_out = nullptr;
+    A.ld_h = ld_h;
+    A.slot_h = slot_h;
+    CK(launch_syrk_tc(A, m, split, std::min(ntiles, g.num_sms), g.stream));
+  } else {
+    CK(launch_syrk_simt(A, ntiles, g.stream));
+  }
+  if (traces_out) {
+    void* hb;
+    CKS(staging(2 * B * sizeof(double) + sizeof(int), &hb));
+    CK(cudaMemcpyAsync(hb, traces, 2 * B * sizeof(double), cudaMemcpyDeviceToHost, g.stream));
+    CK(cudaMemcpyAsync((char*)hb + 2 * B * sizeof(double), err, sizeof(int), cudaMemcpyDeviceToHost, g.stream));
+    CK(cudaStreamSynchronize(g.stream));
+    memcpy(traces_out, hb, 2 * B * sizeof(double));
+    int e = *(int*)((char*)hb + 2 * B * sizeof(double));
+    if (e) {
+      set_err("a bounded device wait timed out");
+      return SP2_ERR_DEVICE_TIMEOUT;
+    }
+  }
+  return SP2_OK;
+}
+
+sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int max_iter, float* D_out,
+                              sp2_stats* stats) {
+  t_err.clear();
+  CKS(require_init());
+  if (!H || !D_out || H == D_out || N < 1 || N > 65536 || N_occ < 0 || N_occ > N || !(tol >= 0.0) ||
+      !std::isfinite(tol) || max_iter < 1 || max_iter > SP2_MAX_LAYERS - 3) {
+    set_err("sp2_density_matrix: invalid argument");
+    return SP2_ERR_INVALID_ARG;
+  }
+  const int prec = g.precision;
+  const bool tc = tc_precision(prec);
+  const bool split = prec == SP2_PREC_SPLIT_FP16;
+  cudaStream_t st = g.stream;
+
+  int ntiles = 0;
+  CKS(upload_tiles(N, 1, tc, &ntiles));
+  void *ctl, *ns, *hs, *dptr, *err, *part, *tick;
+  CKS(ws(B_CTL, sizeof(Ctl), &ctl));
+  CKS(ws(B_NS, sizeof(int), &ns));
+  CKS(ws(B_HS, sizeof(float*), &hs));
+  CKS(ws(B_DPTR, sizeof(float*), &dptr));
+  CKS(ws(B_ERR, sizeof(int), &err, true));
+  const int ggrid = (int)std::min<long long>((N + 7) / 8, 4LL * g.num_sms);
+  const int igrid = (int)std::min<long long>(N, 8LL * g.num_sms);
+  CKS(ws(B_PART, std::max(ggrid, igrid) * sizeof(double2), &part));
+  CKS(ws(B_TICKET, 64 * sizeof(unsigned), &tick, true));
+
+  // small per-call records through pinned staging
+  void* h;
+  CKS(staging(sizeof(Ctl) + 64, &h));
+  Ctl* hc = (Ctl*)h;
+  init_ctl(hc, N, N_occ, tol, max_iter);
+  int* hn = (int*)(hc + 1);
+  hn[0] = N;
+  const float** hh = (const float**)(hn + 2);
+  hh[0] = H;
+  float** hd = (float**)(hh + 1);
+  hd[0] = D_out;
+  CK(cudaMemcpyAsync(ctl, hc, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ns, hn, sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(hs, hh, sizeof(float*), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dptr, hd, sizeof(float*), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(g.stage_done, st));
+
+  SqArgs A;
+  memset(&A, 0, sizeof(A));
+  A.Dptr = (float* const*)dptr;
+  A.Ns = (const int*)ns;
+  A.tiles = (const uint32_t*)g.buf[B_TILES].p;
+  A.ntiles = ntiles;
+  A.tile_off = (const int*)g.buf[B_TOFF].p;
+  A.tile_cnt = (const int*)g.buf[B_TCNT].p;
+  A.ctl = (Ctl*)ctl;
+  A.lp = nullptr;
+  A.tile_part = (double2*)g.buf[B_TPART].p;
+  A.inst_done = (unsigned*)g.buf[B_IDONE].p;
+  A.traces_out = nullptr;
+  A.lo_scale = std::ldexp(1.0f, g.lo_scale_exp);
+  A.lo_unscale = std::ldexp(1.0f, -g.lo_scale_exp);
+  A.err = (int*)err;
+
+  CK(cudaEventRecord(g.ev0, st));
+  CK(launch_gershgorin(H, N, N, (long long)N * N, 1, (double2*)part, (unsigned*)tick, (Ctl*)ctl, nullptr, ggrid, st));
+
+  if (tc) {
+    const long long ld_h = round_up(N, 64), slot_h = ld_h * N;
+    void *hi[2], *lo[2] = {nullptr, nullptr};
+    CKS(ws(B_HI0, (size_t)slot_h * 2, &hi[0]));
+    CKS(ws(B_HI1, (size_t)slot_h * 2, &hi[1]));
+    if (split) {
+      CKS(ws(B_LO0, (size_t)slot_h * 2, &lo[0]));
+      CKS(ws(B_LO1, (size_t)slot_h * 2, &lo[1]));
+    }
+    // K2: Y_0 into D_out, split into buffer 0
+    // Buffers hold N rows of ld_h columns; the tensor maps declare N x N, so
+    // TMA zero-fills every element outside the matrix.
+    CK(launch_input_layer((const float* const*)hs, (const int*)ns, N, D_out, N, (long long)N * N, (__half*)hi[0],
+                          (__half*)lo[0], ld_h, slot_h, N, (int)ld_h, A.lo_scale, (Ctl*)ctl, nullptr, (double2*)part,
+                          (unsigned*)tick, g.shift, 1, 1, igrid, st));
+    CUtensorMap m[2][4];
+    CKS(tmaps_for(hi[0], lo[0], N, 1, ld_h, slot_h, m[0]));
+    CKS(tmaps_for(hi[1], lo[1], N, 1, ld_h, slot_h, m[1]));
+    A.Yin = D_out;
+    A.Yout = D_out;
+    A.ld_y = N;
+    A.slot_y = (long long)N * N;
+    A.ld_h = ld_h;
+    A.slot_h = slot_h;
+    const int grid = std::min(ntiles, g.num_sms);
+    for (int k = 0; k < max_iter + 2; ++k) {
+      const int cur = k & 1;
+      A.hi_out = (__half*)hi[cur ^ 1];
+      A.lo_out = (__half*)lo[cur ^ 1];
+      CK(launch_syrk_tc(A, m[cur], split, grid, st));
+    }
+  } else {
+    const long long ld_y = round_up(N, 4), slot_y = ld_y * N;
+    void* Y[2];
+    CKS(ws(B_Y0, (size_t)slot_y * 4, &Y[0]));
+    CKS(ws(B_Y1, (size_t)slot_y * 4, &Y[1]));
+    CK(launch_input_layer((const float* const*)hs, (const int*)ns, N, (float*)Y[0], ld_y, slot_y, nullptr, nullptr, 0,
+                          0, N, N, A.lo_scale, (Ctl*)ctl, nullptr, (double2*)part, (unsigned*)tick, g.shift, 1, 1, igrid,
+                          st));
+    A.ld_y = ld_y;
+    A.slot_y = slot_y;
+    for (int k = 0; k < max_iter + 2; ++k) {
+      const int cur = k & 1;
+      A.Yin = (float*)Y[cur];
+      A.Yout = (float*)Y[cur ^ 1];
+      CK(launch_syrk_simt(A, ntiles, st));
+    }
+  }
+  CK(cudaEventRecord(g.ev1, st));
+
+  if (!stats) return SP2_OK;
+  void* hb;
+  CKS(staging(sizeof(Ctl) + 16, &hb));
+  CK(cudaMemcpyAsync(hb, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync((char*)hb + sizeof(Ctl), err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, g.ev0, g.ev1));
+  const Ctl& c = *(const Ctl*)hb;
+  const int e = *(const int*)((char*)hb + sizeof(Ctl));
+  fill_stats(c, stats, ms, prec);
+  return status_of(c, e);
+}
+
+sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const int* N_occ, int batch, double tol,
+                                      int max_iter, float* const* D_out, sp2_stats* stats) {
+  (void)H; (void)N; (void)N_occ; (void)batch; (void)tol; (void)max_iter; (void)D_out; (void)stats;
+  set_err("sp2_density_matrix_batched: not available in this build");
+  return SP2_ERR_UNSUPPORTED;
+}
+
+sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float* coef, int ckpt_every, float* X_out,
+                               float* ckpt, double* bounds) {
+  (void)H; (void)B; (void)N; (void)L; (void)coef; (void)ckpt_every; (void)X_out; (void)ckpt; (void)bounds;
+  set_err("sp2_network_forward: not available in this build");
+  return SP2_ERR_UNSUPPORTED;
+}
+
+sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float* coef, int ckpt_every,
+                                const float* ckpt, const float* G_out, double* dcoef, float* G_in) {
+  (void)H; (void)B; (void)N; (void)L; (void)coef; (void)ckpt_every; (void)ckpt; (void)G_out; (void)dcoef; (void)G_in;
+  set_err("sp2_network_backward: not available in this build");
+  return SP2_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,194 @@
+// Shared device-side definitions of the SP2 library (sm_103a).
+//
+// The iterate of Alg. 1 is stored as S = alpha I + Y with an FP64 scalar
+// alpha kept on the device and Y in FP32 (plus its FP16 hi/lo split).  With
+// the shift disabled alpha stays 0 and Y = S.  Both branches of the SP2
+// layer (Eq. 10 / Alg. 1, W_n = sigma_n I, B_n = (I - W_n) S_{n-1}) and the
+// generalised layer of Eq. 16 map onto the same element-wise epilogue
+//     Y' = ca * Y + cb * P + cc * I,   P = Y^2 (tensor cores or FFMA),
+// with the identity part carried in alpha:
+//     S^2 = alpha^2 I + 2 alpha Y + Y^2,
+//     sigma = +1: alpha' = alpha^2,            ca = 2 alpha,     cb = +1
+//     sigma = -1: alpha' = 2 alpha - alpha^2,  ca = 2 - 2 alpha, cb = -1
+// and traces  tr S = N alpha + tr Y,
+//             Tr[S^2] = ||S||_F^2 = N alpha^2 + 2 alpha tr Y + ||Y||_F^2.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sp2.h"
+
+namespace sp2 {
+
+constexpr int kMaxL = SP2_MAX_LAYERS;
+
+enum OutMode : int { OUT_Y = 0, OUT_D = 1 };
+enum Phase : int { PHASE_LOOP = 0, PHASE_REFINE_A = 1, PHASE_REFINE_B = 2, PHASE_DONE = 3, PHASE_ERROR = 4 };
+
+// Coefficients of one squaring launch.  Written either by the host (network
+// and single-layer entry points) or by the device control step (SP2 loop).
+struct LayerParams {
+  float ca, cb, cc;   // Y' = ca Y + cb P + cc I
+  float alpha_out;    // OUT_D: D = Y' + alpha_out I
+  int active;         // 0: the launch does nothing (converged / finished)
+  int out_mode;       // OutMode
+  int pad0, pad1;
+};
+
+// Device-resident state of one SP2 solve (Alg. 1 scalars, FP64).
+struct Ctl {
+  // configuration
+  int N, max_iter, n_occ, shift;
+  double tol, eps;
+  // state
+  int phase, n, stop_pending, converged_by;
+  int status, sigma_a, pad0, pad1;
+  double alpha, alpha_next;   // shift of the stored iterate / of the one being computed
+  double trY, sqY;            // tr Y, ||Y||_F^2 of the stored Y
+  double e_min, e_max;
+  double trace_final;
+  LayerParams next;           // parameters of the next squaring launch
+  int sigma[kMaxL + 1];       // sigma[k] = sigma_k, sigma[0] = 0
+  double iderr[kMaxL + 1];    // iderr[k] = IdErr_k
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ void split_fp16(float x, float lo_scale, __half& hi, __half& lo) {
+  // Eq. 12: hi = FP16[x], lo = FP16[2^s (x - hi)]; x - hi is exact in FP32.
+  hi = __float2half_rn(x);
+  lo = __float2half_rn((x - __half2float(hi)) * lo_scale);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Branch sigma applied to the stored iterate: sets alpha_next and the launch
+// coefficients (see the header comment).
+__device__ inline void set_branch(Ctl* c, int sigma, bool final_layer) {
+  const double a = c->alpha;
+  double an, ca, cb;
+  if (sigma > 0) {
+    an = a * a;
+    ca = 2.0 * a;
+    cb = 1.0;
+  } else {
+    an = 2.0 * a - a * a;
+    ca = 2.0 - 2.0 * a;
+    cb = -1.0;
+  }
+  c->alpha_next = an;
+  LayerParams p;
+  p.ca = (float)ca;
+  p.cb = (float)cb;
+  p.cc = 0.f;
+  p.alpha_out = final_layer ? (float)an : 0.f;
+  p.active = 1;
+  p.out_mode = final_layer ? OUT_D : OUT_Y;
+  p.pad0 = p.pad1 = 0;
+  c->next = p;
+}
+
+// Control step of Alg. 1, run by one thread after the launch that stored a
+// new iterate (the input layer for n = 0).  trY / sqY are the FP64 sums of
+// the Y just stored.  Decides sigma_{n+1}, IdErr_{n+1} and the stop rules
+// (IdErr <= tol, IdErr <= 0, the 4.5 rule after a sign change, max_iter), or
+// moves on to the two refinement layers of Eq. 15.
+__device__ inline void control_step(Ctl* c, double trY, double sqY) {
+  c->trY = trY;
+  c->sqY = sqY;
+  c->alpha = c->alpha_next;
+  const double N = (double)c->N;
+  if (c->phase == PHASE_LOOP) {
+    if (c->stop_pending) {
+      int s = (c->n >= 3) ? c->sigma[c->n - 2] : 1;  // f_final order from sigma_{n-2}
+      s = (s >= 0) ? 1 : -1;
+      c->sigma_a = s;
+      c->phase = PHASE_REFINE_A;
+      set_branch(c, s, false);
+      return;
+    }
+    const int n1 = c->n + 1;
+    const double a = c->alpha;
+    const double NS = N * a + trY;                      // Tr[S_n]
+    const double NX = N * a * a + 2.0 * a * trY + sqY;  // Tr[S_n^2] = ||S_n||_F^2
+    const double err = N * a * (1.0 - a) + (1.0 - 2.0 * a) * trY - sqY;  // N_S - N_X
+    const double no = (double)c->n_occ;
+    const double v = fabs(2.0 * NS - NX - no) - fabs(NX - no) - (double)c->sigma[c->n] * c->eps;
+    const int s = (v >= 0.0) ? 1 : -1;
+    c->sigma[n1] = s;
+    c->iderr[n1] = err;
+    int stop = SP2_STOP_NONE;
+    if (c->tol > 0.0 && err <= c->tol)
+      stop = SP2_STOP_TOL;
+    else if (err <= 0.0)
+      stop = SP2_STOP_IDERR;
+    else if (n1 > 2 && c->sigma[n1 - 1] != c->sigma[n1 - 2] && err > 4.5 * c->iderr[n1 - 2] * c->iderr[n1 - 2])
+      stop = SP2_STOP_RULE45;
+    else if (n1 >= c->max_iter)
+      stop = SP2_STOP_MAXITER;
+    c->n = n1;
+    c->stop_pending = stop;
+    if (stop) c->converged_by = stop;
+    set_branch(c, s, false);
+  } else if (c->phase == PHASE_REFINE_A) {
+    c->phase = PHASE_REFINE_B;
+    set_branch(c, -c->sigma_a, true);
+  } else if (c->phase == PHASE_REFINE_B) {
+    c->trace_final = N * c->alpha + trY;
+    c->phase = PHASE_DONE;
+    c->next.active = 0;
+    if (c->status == SP2_OK && c->converged_by == SP2_STOP_MAXITER) c->status = SP2_NOT_CONVERGED;
+  }
+}
+
+// Per-launch reduction of FP64 partials with a last-block ticket: every CTA
+// stores its (trY, sqY) partial, the CTA that arrives last sums them in a
+// fixed order (deterministic) and returns true.  No CTA waits on another.
+__device__ inline bool last_block_reduce(double tr, double sq, double2* partials, unsigned* ticket,
+                                         double& tr_out, double& sq_out) {
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = make_double2(tr, sq);
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    double a = 0.0, b = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += 32) {
+      const double2 p = __ldcg(&partials[i]);
+      a += p.x;
+      b += p.y;
+    }
+    a = warp_sum_d(a);
+    b = warp_sum_d(b);
+    if (threadIdx.x == 0) {
+      tr_out = a;
+      sq_out = b;
+      *ticket = 0u;
+    }
+  }
+  return threadIdx.x == 0;
+}
+
+// Tile descriptor of the squaring kernels: instance b, block row I, block
+// column J (I <= J in units of the kernel's tile), and sub-row h.
+__host__ __device__ inline uint32_t pack_tile(int b, int I, int J, int h) {
+  return ((uint32_t)b << 20) | ((uint32_t)I << 11) | ((uint32_t)J << 2) | (uint32_t)h;
+}
+__host__ __device__ inline void unpack_tile(uint32_t t, int& b, int& I, int& J, int& h) {
+  b = (int)(t >> 20);
+  I = (int)((t >> 11) & 0x1FF);
+  J = (int)((t >> 2) & 0x1FF);
+  h = (int)(t & 3);
+}
+
+}  // namespace sp2

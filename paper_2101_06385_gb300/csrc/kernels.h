@@ -1,0 +1,76 @@
+// Host-side launch interface of the SP2 kernels (internal to libsp2.so).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace sp2 {
+
+// Arguments shared by the squaring kernels (FFMA and tcgen05).
+//
+// Storage of instance b (0 <= b < batch) with size n_b = Ns[b]:
+//   Y      FP32 iterate, element (r, c) at Y + b*slot_y + r*ld_y + c
+//   hi/lo  FP16 split of Y (tensor-core path), b*slot_h + r*ld_h + c; the
+//          region [n_b, ld) of every row and rows >= n_b stay zero
+//   Dptr   per-instance final outputs [n_b, n_b] (ld n_b), used by OUT_D
+// Tiles: tiles[t] packs (b, I, J, h); the tiles of one instance are
+// contiguous, starting at tile_off[b], tile_cnt[b] of them.
+struct SqArgs {
+  const float* Yin;        // FFMA path: operand and old value (read-only)
+  float* Yout;             // updated iterate (may equal Yin on the tensor-core path)
+  long long ld_y, slot_y;
+  __half* hi_out;          // split of the updated iterate (nullptr: not written)
+  __half* lo_out;
+  long long ld_h, slot_h;
+  float* const* Dptr;      // [batch] device array of output pointers (OUT_D)
+  const int* Ns;           // [batch]
+  const uint32_t* tiles;   // [ntiles]
+  int ntiles;
+  const int* tile_off;     // [batch]
+  const int* tile_cnt;     // [batch]
+  Ctl* ctl;                // [batch] control blocks, or nullptr
+  const LayerParams* lp;   // coefficients when ctl == nullptr
+  int lp_per_instance;     // 1: lp[b] per instance, 0: lp[0] shared by the batch
+  double2* tile_part;      // [ntiles] per-tile (tr, sq) partials
+  unsigned* inst_done;     // [batch] tile-completion counters (zero between launches)
+  double* traces_out;      // [batch][2] when ctl == nullptr, or nullptr
+  float lo_scale;          // 2^s
+  float lo_unscale;        // 2^-s
+  int* err;                // device error word (SP2_ERR_DEVICE_TIMEOUT on a timed-out wait)
+};
+
+// tensor-core tile geometry
+constexpr int kTcBM = 128;   // rows per CTA tile (TMEM lanes)
+constexpr int kTcBN = 256;   // columns per CTA tile; 256 x 256 "super tiles" hold two CTA tiles
+constexpr int kSimtB = 128;  // FFMA tile
+
+cudaError_t launch_gershgorin(const float* H, int N, long long ld, long long slot, int B, double2* partials,
+                              unsigned* ticket, Ctl* ctl, double* bounds_out, int grid, cudaStream_t st);
+cudaError_t launch_gershgorin_batched(const float* const* Hs, const int* Ns, Ctl* ctl, int batch, cudaStream_t st);
+cudaError_t launch_input_layer(const float* const* Hs, const int* Ns, long long ld_in, float* Y, long long ld_y,
+                               long long slot_y, __half* hi, __half* lo, long long ld_h, long long slot_h, int rows_pad,
+                               int cols_pad, float lo_scale, Ctl* ctl, const double* bounds, double2* partials, unsigned* tickets,
+                               int shift, int ctl_step, int batch, int grid_x, cudaStream_t st);
+cudaError_t launch_split(const float* X, long long n, float lo_scale, __half* hi, __half* lo, int grid,
+                         cudaStream_t st);
+cudaError_t launch_split_pad(const float* X, long long ld_x, long long slot_x, int N, int B, float lo_scale,
+                             __half* hi, __half* lo, long long ld_h, long long slot_h, int grid, cudaStream_t st);
+cudaError_t launch_observable(const float* D, const float* A, long long n, double* block_out, int grid,
+                              cudaStream_t st);
+
+cudaError_t launch_syrk_simt(const SqArgs& a, int grid, cudaStream_t st);
+
+// Tensor-core squaring.  tmaps: {hi(A box), lo(A box), hi(B box), lo(B box)}
+// over the current split buffers.  split = false: plain FP16 (hi only).
+cudaError_t launch_syrk_tc(const SqArgs& a, const CUtensorMap* tmaps, bool split, int grid, cudaStream_t st);
+size_t syrk_tc_smem_bytes(bool split);
+
+// Encodes a 3D tensor map over FP16 [batch][rows][ld] with box {box_k, box_rows, 1}.
+bool make_tmap_f16(CUtensorMap* out, const void* base, int cols, int rows, int batch, long long ld, long long slot,
+                   int box_k, int box_rows);
+
+}  // namespace sp2

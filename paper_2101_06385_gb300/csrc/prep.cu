@@ -1,0 +1,378 @@
+// Memory-bound kernels of the SP2 path (sm_103a):
+//   K1 gershgorin_kernel   spectral bound estimates (Alg. 1 inputs), FP64
+//   K2 input_layer_kernel  S_0 = W_0 H + B_0 (Alg. 1), stored as alpha_0 I + Y_0,
+//                          FP16 split of Y_0 (Eq. 12), FP64 trace partials,
+//                          then the first control step (sigma_1, IdErr_1)
+//      split_kernel        stand-alone split (Eq. 12)
+//      observable_kernel   Tr[D A] (Alg. 1, last line)
+//      network prologue    the same input layer for a batch, no control
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sp2 {
+
+// ---------------------------------------------------------------- K1
+// One warp per row: R_i = sum_j |H_ij| - |H_ii|.  Float4 groups are summed
+// in FP32 (two additions) and accumulated in FP64.  Per-block min/max, then
+// the last block folds all blocks and writes the bounds into each
+// instance's control block (or bounds_out).
+__global__ void __launch_bounds__(256) gershgorin_kernel(const float* __restrict__ H, int N, long long ld,
+                                                         long long slot, int B, double2* __restrict__ partials,
+                                                         unsigned* __restrict__ ticket, Ctl* ctl,
+                                                         double* bounds_out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long rows_total = (long long)N * B;
+  double lo = INFINITY, hi = -INFINITY;
+  const bool vec = ((ld & 3) == 0) && ((((uintptr_t)H) & 15) == 0);
+  bool bad = false;
+  for (long long gr = (long long)blockIdx.x * 8 + warp; gr < rows_total; gr += (long long)gridDim.x * 8) {
+    const int b = (int)(gr / N), i = (int)(gr % N);
+    const float* row = H + (long long)b * slot + (long long)i * ld;
+    double acc = 0.0;
+    if (vec) {
+      const float4* r4 = reinterpret_cast<const float4*>(row);
+      const int n4 = N >> 2;
+      for (int j = lane; j < n4; j += 32) {
+        const float4 v = __ldcs(r4 + j);
+        acc += (double)((fabsf(v.x) + fabsf(v.y)) + (fabsf(v.z) + fabsf(v.w)));
+      }
+      for (int j = (n4 << 2) + lane; j < N; j += 32) acc += (double)fabsf(row[j]);
+    } else {
+      for (int j = lane; j < N; j += 32) acc += (double)fabsf(row[j]);
+    }
+    acc = warp_sum_d(acc);
+    const double d = (double)row[i];
+    const double R = acc - fabs(d);
+    if (!isfinite(R) || !isfinite(d)) bad = true;  // fmin/fmax would drop a NaN
+    lo = fmin(lo, d - R);
+    hi = fmax(hi, d + R);
+  }
+  __shared__ double s_lo[8], s_hi[8];
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  if (lane == 0) {
+    s_lo[warp] = lo;
+    s_hi[warp] = hi;
+    if (bad) atomicOr(&s_bad, 1);
+  }
+  __syncthreads();
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < 8; ++w) {
+      lo = fmin(lo, s_lo[w]);
+      hi = fmax(hi, s_hi[w]);
+    }
+    if (s_bad) lo = hi = NAN;
+    partials[blockIdx.x] = make_double2(lo, hi);
+    __threadfence();
+    s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double L = INFINITY, U = -INFINITY;
+  bool nonfinite = false;
+  for (unsigned k = 0; k < gridDim.x; ++k) {
+    const double2 p = __ldcg(&partials[k]);
+    if (isnan(p.x) || isnan(p.y)) nonfinite = true;
+    L = fmin(L, p.x);
+    U = fmax(U, p.y);
+  }
+  if (isnan(L) || isnan(U)) nonfinite = true;
+  *ticket = 0u;
+  if (bounds_out) {
+    bounds_out[0] = nonfinite ? NAN : L;
+    bounds_out[1] = nonfinite ? NAN : U;
+  }
+  if (ctl) {
+    // single-instance path (B == 1)
+    Ctl* c = ctl;
+    c->e_min = L;
+    c->e_max = U;
+    if (nonfinite || !isfinite(L) || !isfinite(U)) {
+      c->status = SP2_ERR_NONFINITE;
+      c->phase = PHASE_ERROR;
+      c->next.active = 0;
+    } else if (!(U - L > 0.0)) {
+      if (c->n_occ == 0 || c->n_occ == c->N) {
+        // H = cI: any enclosing interval is a valid bound estimate
+        c->e_min = L - 1.0;
+        c->e_max = U + 1.0;
+      } else {
+        c->status = SP2_ERR_DEGENERATE_SPECTRUM;
+        c->phase = PHASE_ERROR;
+        c->next.active = 0;
+      }
+    }
+  }
+}
+
+// Per-instance Gershgorin for the batched path: one block per instance
+// (instances are small), results into ctl[b].
+__global__ void __launch_bounds__(256) gershgorin_batched_kernel(const float* const* __restrict__ Hs,
+                                                                 const int* __restrict__ Ns, Ctl* __restrict__ ctl) {
+  const int b = blockIdx.x;
+  const int N = Ns[b];
+  const float* H = Hs[b];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double lo = INFINITY, hi = -INFINITY;
+  bool bad = false;
+  for (int i = warp; i < N; i += 8) {
+    const float* row = H + (long long)i * N;
+    double acc = 0.0;
+    for (int j = lane; j < N; j += 32) acc += (double)fabsf(row[j]);
+    acc = warp_sum_d(acc);
+    const double d = (double)row[i];
+    const double R = acc - fabs(d);
+    if (!isfinite(R) || !isfinite(d)) bad = true;
+    lo = fmin(lo, d - R);
+    hi = fmax(hi, d + R);
+  }
+  __shared__ double s_lo[8], s_hi[8];
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  if (lane == 0) {
+    s_lo[warp] = lo;
+    s_hi[warp] = hi;
+    if (bad) atomicOr(&s_bad, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double L = INFINITY, U = -INFINITY;
+  bool nan_seen = s_bad != 0;
+  for (int w = 0; w < 8; ++w) {
+    L = fmin(L, s_lo[w]);
+    U = fmax(U, s_hi[w]);
+  }
+  Ctl* c = ctl + b;
+  c->e_min = L;
+  c->e_max = U;
+  if (nan_seen || !isfinite(L) || !isfinite(U)) {
+    c->status = SP2_ERR_NONFINITE;
+    c->phase = PHASE_ERROR;
+    c->next.active = 0;
+  } else if (!(U - L > 0.0)) {
+    if (c->n_occ == 0 || c->n_occ == c->N) {
+      c->e_min = L - 1.0;
+      c->e_max = U + 1.0;
+    } else {
+      c->status = SP2_ERR_DEGENERATE_SPECTRUM;
+      c->phase = PHASE_ERROR;
+      c->next.active = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- K2
+// Input layer for one instance (b = blockIdx.y): y = (shift ? -h : (e_max d_ij - h)) / (e_max - e_min)
+// written as FP32 into Y (ld_y, slot_y) and as the FP16 split into hi/lo
+// (ld_h, slot_h; padding up to Npad zero-filled).  FP64 partials (tr Y,
+// ||Y||_F^2) and, when ctl_step, the first control step by the last block.
+__global__ void __launch_bounds__(256) input_layer_kernel(const float* const* __restrict__ Hs,
+                                                          const int* __restrict__ Ns, long long ld_in_fixed,
+                                                          float* __restrict__ Y, long long ld_y, long long slot_y,
+                                                          __half* __restrict__ hi, __half* __restrict__ lo,
+                                                          long long ld_h, long long slot_h, int rows_pad, int cols_pad,
+                                                          float lo_scale,
+                                                          Ctl* __restrict__ ctl, const double* __restrict__ bounds,
+                                                          double2* __restrict__ partials, unsigned* __restrict__ tickets,
+                                                          int shift, int ctl_step) {
+  const int b = blockIdx.y;
+  const int N = Ns[b];
+  const float* H = Hs[b];
+  const long long ld_in = ld_in_fixed > 0 ? ld_in_fixed : N;
+  double e_min, e_max;
+  bool active = true;
+  if (ctl) {
+    const Ctl* c = ctl + b;
+    active = (c->phase != PHASE_ERROR);
+    e_min = c->e_min;
+    e_max = c->e_max;
+  } else {
+    e_min = bounds[2 * b];
+    e_max = bounds[2 * b + 1];
+  }
+  const double inv = 1.0 / (e_max - e_min);
+  const double diag_add = shift ? 0.0 : e_max * inv;
+  double tr = 0.0, sq = 0.0;
+  if (active) {
+    const int rows = (hi != nullptr) ? rows_pad : N;
+    const int cols = (hi != nullptr) ? cols_pad : N;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+      const float* hrow = H + (long long)r * ld_in;
+      float* yrow = Y + (long long)b * slot_y + (long long)r * ld_y;
+      __half* hirow = hi ? hi + (long long)b * slot_h + (long long)r * ld_h : nullptr;
+      __half* lorow = hi ? lo + (long long)b * slot_h + (long long)r * ld_h : nullptr;
+      float sqf = 0.f;
+      for (int col = threadIdx.x; col < cols; col += blockDim.x) {
+        float y = 0.f;
+        if (r < N && col < N) {
+          double v = -(double)hrow[col] * inv;
+          if (r == col) v += diag_add;
+          y = (float)v;
+          yrow[col] = y;
+          if (r == col) tr += (double)y;
+          sqf = fmaf(y, y, sqf);
+        }
+        if (hirow) {
+          __half h16, l16;
+          split_fp16(y, lo_scale, h16, l16);
+          hirow[col] = h16;
+          lorow[col] = l16;
+        }
+      }
+      sq += (double)sqf;
+    }
+  }
+  tr = warp_sum_d(tr);
+  sq = warp_sum_d(sq);
+  __shared__ double s_tr[8], s_sq[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_tr[warp] = tr;
+    s_sq[warp] = sq;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tr = 0.0;
+    sq = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      tr += s_tr[w];
+      sq += s_sq[w];
+    }
+  }
+  if (!ctl_step || ctl == nullptr) return;
+  // last-block reduction per instance
+  __shared__ bool s_last;
+  double2* part = partials + (long long)b * gridDim.x;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = make_double2(tr, sq);
+    __threadfence();
+    s_last = (atomicAdd(&tickets[b], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double T = 0.0, Q = 0.0;
+  for (unsigned k = 0; k < gridDim.x; ++k) {
+    const double2 p = __ldcg(&part[k]);
+    T += p.x;
+    Q += p.y;
+  }
+  tickets[b] = 0u;
+  Ctl* c = ctl + b;
+  if (!active) return;
+  c->alpha_next = shift ? e_max * inv : 0.0;
+  control_step(c, T, Q);
+}
+
+// ---------------------------------------------------------------- split
+__global__ void split_kernel(const float* __restrict__ X, long long n, float lo_scale, __half* __restrict__ hi,
+                             __half* __restrict__ lo) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    __half h, l;
+    split_fp16(X[i], lo_scale, h, l);
+    hi[i] = h;
+    lo[i] = l;
+  }
+}
+
+// ---------------------------------------------------------------- split, padded
+// X [B][N][ld_x] FP32 -> hi/lo [B][N][ld_h] FP16 with the row tail [N, ld_h) zeroed.
+__global__ void split_pad_kernel(const float* __restrict__ X, long long ld_x, long long slot_x, int N, int B,
+                                 float lo_scale, __half* __restrict__ hi, __half* __restrict__ lo, long long ld_h,
+                                 long long slot_h) {
+  const long long rows = (long long)N * B;
+  for (long long gr = blockIdx.x; gr < rows; gr += gridDim.x) {
+    const int b = (int)(gr / N), r = (int)(gr % N);
+    const float* xr = X + (long long)b * slot_x + (long long)r * ld_x;
+    __half* hr = hi + (long long)b * slot_h + (long long)r * ld_h;
+    __half* lr = lo ? lo + (long long)b * slot_h + (long long)r * ld_h : nullptr;
+    for (int c = threadIdx.x; c < (int)ld_h; c += blockDim.x) {
+      const float x = (c < N) ? xr[c] : 0.f;
+      __half h, l;
+      split_fp16(x, lo_scale, h, l);
+      hr[c] = h;
+      if (lr) lr[c] = l;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- observable
+__global__ void __launch_bounds__(256) observable_kernel(const float* __restrict__ D, const float* __restrict__ A,
+                                                         long long n, double* __restrict__ block_out) {
+  double acc = 0.0;
+  const bool vec = ((((uintptr_t)D) | ((uintptr_t)A)) & 15) == 0;
+  if (vec) {
+    const long long n4 = n >> 2;
+    const float4* D4 = reinterpret_cast<const float4*>(D);
+    const float4* A4 = reinterpret_cast<const float4*>(A);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+      const float4 d = __ldcs(D4 + i), a = __ldcs(A4 + i);
+      acc += (double)d.x * a.x + (double)d.y * a.y + (double)d.z * a.z + (double)d.w * a.w;
+    }
+    for (long long i = (n4 << 2) + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+      acc += (double)D[i] * A[i];
+  } else {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+      acc += (double)D[i] * A[i];
+  }
+  acc = warp_sum_d(acc);
+  __shared__ double s[8];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    block_out[blockIdx.x] = t;
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_gershgorin(const float* H, int N, long long ld, long long slot, int B, double2* partials,
+                              unsigned* ticket, Ctl* ctl, double* bounds_out, int grid, cudaStream_t st) {
+  gershgorin_kernel<<<grid, 256, 0, st>>>(H, N, ld, slot, B, partials, ticket, ctl, bounds_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gershgorin_batched(const float* const* Hs, const int* Ns, Ctl* ctl, int batch, cudaStream_t st) {
+  gershgorin_batched_kernel<<<batch, 256, 0, st>>>(Hs, Ns, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_input_layer(const float* const* Hs, const int* Ns, long long ld_in, float* Y, long long ld_y,
+                               long long slot_y, __half* hi, __half* lo, long long ld_h, long long slot_h, int rows_pad,
+                               int cols_pad, float lo_scale, Ctl* ctl, const double* bounds, double2* partials, unsigned* tickets,
+                               int shift, int ctl_step, int batch, int grid_x, cudaStream_t st) {
+  dim3 grid(grid_x, batch);
+  input_layer_kernel<<<grid, 256, 0, st>>>(Hs, Ns, ld_in, Y, ld_y, slot_y, hi, lo, ld_h, slot_h, rows_pad, cols_pad,
+                                           lo_scale, ctl,
+                                           bounds, partials, tickets, shift, ctl_step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split(const float* X, long long n, float lo_scale, __half* hi, __half* lo, int grid,
+                         cudaStream_t st) {
+  split_kernel<<<grid, 256, 0, st>>>(X, n, lo_scale, hi, lo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_pad(const float* X, long long ld_x, long long slot_x, int N, int B, float lo_scale,
+                             __half* hi, __half* lo, long long ld_h, long long slot_h, int grid, cudaStream_t st) {
+  split_pad_kernel<<<grid, 256, 0, st>>>(X, ld_x, slot_x, N, B, lo_scale, hi, lo, ld_h, slot_h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_observable(const float* D, const float* A, long long n, double* block_out, int grid,
+                              cudaStream_t st) {
+  observable_kernel<<<grid, 256, 0, st>>>(D, A, n, block_out);
+  return cudaGetLastError();
+}
+
+}  // namespace sp2

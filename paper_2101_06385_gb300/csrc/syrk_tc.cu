@@ -1,0 +1,536 @@
+// Split-FP16 symmetric squaring on the 5th-generation tensor cores (sm_103a):
+// tcgen05.mma with FP32 accumulators in tensor memory, operands staged in
+// shared memory by TMA, fused SP2 layer epilogue.
+//
+// Alg. 2 / Eq. 14: with Y ~ hi + 2^-s lo (Eq. 12, lo scaled by 2^s),
+//     P = Y^2 ~ hi hi + 2^-s (lo hi + hi lo)          (the lo lo term is dropped)
+// Y is symmetric, so tile (I, J) of P is  sum_k Y[I, k] Y[J, k]^T: both MMA
+// operands are row panels in K-major layout.  Only the upper 256 x 256 super
+// tiles (I <= J) are computed (the symmetric-half remark under Eq. 14); each
+// is two 128 x 256 CTA tiles.  Off-diagonal super tiles are stored twice
+// (mirrored) so every layer again reads full row panels.
+//
+// CTA = 6 warps, persistent over a static tile list:
+//   warp 0      TMA producer (one thread): hi/lo of rows I (128) and J (256)
+//   warp 1      TMEM allocation + MMA issuer (one thread)
+//   warps 2..5  epilogue: TMEM -> registers, Y' = ca Y + cb P + cc I,
+//               re-split to hi/lo, mirrored stores, FP64 trace partials
+// TMEM: ACC0 = hi hi in columns [0, 256), ACC1 = lo hi + hi lo in [256, 512).
+// Every mbarrier wait is bounded (globaltimer); on time-out the CTA records
+// SP2_ERR_DEVICE_TIMEOUT, stops issuing, drains and frees its TMEM.
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tile_finish.cuh"
+
+namespace sp2 {
+
+namespace tc {
+
+constexpr int BM = kTcBM;           // 128
+constexpr int BN = kTcBN;           // 256
+constexpr int BK = 32;              // K per stage: 32 FP16 = 64 B rows (64-byte swizzle)
+constexpr int UMMA_K = 16;          // K per tcgen05.mma (kind::f16)
+constexpr int A_BYTES = BM * BK * 2;   // 8 KB
+constexpr int B_BYTES = BN * BK * 2;   // 16 KB
+constexpr int STAGE_SPLIT = 2 * A_BYTES + 2 * B_BYTES;  // 48 KB: hiA loA hiB loB
+constexpr int STAGE_PLAIN = A_BYTES + B_BYTES;          // 24 KB: hiA hiB
+constexpr int STAGES_SPLIT = 4;
+constexpr int STAGES_PLAIN = 8;
+constexpr int THREADS = 192;
+constexpr unsigned long long kTimeoutNs = 4000000000ull;  // 4 s
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = F16
+// (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false on time-out or when another warp of the CTA aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > kTimeoutNs) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major operand, 64-byte
+// swizzle, rows of 64 B, 8-row core groups 512 B apart.
+//   bits  0-13 start address >> 4
+//   bits 16-29 leading byte offset >> 4 (not used by swizzled K-major; 1)
+//   bits 32-45 stride byte offset >> 4 (512 B)
+//   bits 46-47 descriptor version (1 on sm_100-class parts)
+//   bits 61-63 swizzle mode (4 = 64-byte)
+__device__ __forceinline__ uint64_t make_desc_sw64(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(512u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)4u << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 lanes x 32 consecutive FP32 columns: thread i of the warp gets its lane's row.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ LayerParams load_params(const SqArgs& a, int b) {
+  return a.ctl ? a.ctl[b].next : a.lp[a.lp_per_instance ? b : 0];
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(THREADS, 1)
+    syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_hiA, const __grid_constant__ CUtensorMap tm_loA,
+                   const __grid_constant__ CUtensorMap tm_hiB, const __grid_constant__ CUtensorMap tm_loB,
+                   const SqArgs a) {
+  constexpr int STAGES = SPLIT ? STAGES_SPLIT : STAGES_PLAIN;
+  constexpr int STAGE_BYTES = SPLIT ? STAGE_SPLIT : STAGE_PLAIN;
+  constexpr uint32_t TMEM_COLS = SPLIT ? 512 : 256;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tmem_full = empty + STAGES;
+  uint64_t* tmem_empty = tmem_full + 1;
+  uint64_t* drain = tmem_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  __shared__ int s_abort;
+  __shared__ double s_red[4][2];
+  __shared__ int s_got[4];
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tmem_full, 1);
+    mbar_init(tmem_empty, 4);
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      uint32_t armed[STAGES];
+#pragma unroll
+      for (int s = 0; s < STAGES; ++s) armed[s] = 0;
+      for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        int b, I, J, h;
+        unpack_tile(a.tiles[t], b, I, J, h);
+        if (!load_params(a, b).active) continue;
+        const int N = a.Ns[b];
+        const int rowA = I * BN + h * BM, rowB = J * BN;
+        const int nk = (N + BK - 1) / BK;
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + stage * STAGE_BYTES;
+          mbar_expect_tx(&full[stage], STAGE_BYTES);
+          const int k0 = kb * BK;
+          if (SPLIT) {
+            tma_load_3d(st, &tm_hiA, k0, rowA, b, &full[stage]);
+            tma_load_3d(st + A_BYTES, &tm_loA, k0, rowA, b, &full[stage]);
+            tma_load_3d(st + 2 * A_BYTES, &tm_hiB, k0, rowB, b, &full[stage]);
+            tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tm_loB, k0, rowB, b, &full[stage]);
+          } else {
+            tma_load_3d(st, &tm_hiA, k0, rowA, b, &full[stage]);
+            tma_load_3d(st + A_BYTES, &tm_hiB, k0, rowB, b, &full[stage]);
+          }
+          ++armed[stage];
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok || *abort_flag) {
+        atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
+        // Drain: the copies this thread issued land before the CTA exits
+        // (the k-th arming of a stage completes the phase of parity (k-1)&1).
+        for (int s = 0; s < STAGES; ++s) {
+          if (armed[s] == 0) continue;
+          const uint64_t t0 = globaltimer();
+          while (!mbar_try_wait(&full[s], (armed[s] - 1u) & 1u) && globaltimer() - t0 < kTimeoutNs) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, acc_phase = 0;
+      bool ok = true;
+      bool issued = false;
+      for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        int b, I, J, h;
+        unpack_tile(a.tiles[t], b, I, J, h);
+        if (!load_params(a, b).active) continue;
+        const int N = a.Ns[b];
+        const int nk = (N + BK - 1) / BK;
+        if (!mbar_wait(tmem_empty, acc_phase ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        acc_phase ^= 1u;
+        tc_fence_after();
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!mbar_wait(&full[stage], phase, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + stage * STAGE_BYTES);
+#pragma unroll
+          for (int ks = 0; ks < BK / UMMA_K; ++ks) {
+            const uint32_t koff = ks * UMMA_K * 2;  // bytes within the 64-byte row
+            const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
+            if (SPLIT) {
+              const uint64_t dhiA = make_desc_sw64(st + koff);
+              const uint64_t dloA = make_desc_sw64(st + A_BYTES + koff);
+              const uint64_t dhiB = make_desc_sw64(st + 2 * A_BYTES + koff);
+              const uint64_t dloB = make_desc_sw64(st + 2 * A_BYTES + B_BYTES + koff);
+              mma_f16(tmem_base, dhiA, dhiB, acc);              // ACC0 += hi_I hi_J^T
+              mma_f16(tmem_base + BN, dloA, dhiB, acc);         // ACC1 += lo_I hi_J^T
+              mma_f16(tmem_base + BN, dhiA, dloB, 1u);          // ACC1 += hi_I lo_J^T
+            } else {
+              const uint64_t dhiA = make_desc_sw64(st + koff);
+              const uint64_t dhiB = make_desc_sw64(st + A_BYTES + koff);
+              mma_f16(tmem_base, dhiA, dhiB, acc);
+            }
+          }
+          mma_commit(&empty[stage]);
+          issued = true;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        mma_commit(tmem_full);
+      }
+      if (!ok) atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
+      if (issued) {
+        // all MMAs of this CTA have completed once this commit lands
+        mma_commit(drain);
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;                 // TMEM lane quarter of this warp
+    const int row_local = q * 32 + lane;
+    uint32_t acc_phase = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+      int b, I, J, h;
+      unpack_tile(a.tiles[t], b, I, J, h);
+      const LayerParams p = load_params(a, b);
+      if (!p.active) continue;
+      const int N = a.Ns[b];
+      const int r = I * BN + h * BM + row_local;
+      const int cb0 = J * BN;
+      const bool mirror = (I != J);
+      const bool outD = (p.out_mode == OUT_D);
+      const bool got = mbar_wait(tmem_full, acc_phase, abort_flag);
+      // the four epilogue warps take one decision: go on only if all of them
+      // saw the accumulator arrive (s_got is rewritten only after the
+      // end-of-tile barriers below)
+      if (lane == 0) s_got[q] = got ? 1 : 0;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (!(s_got[0] & s_got[1] & s_got[2] & s_got[3])) {
+        if (!got && lane == 0) atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
+        break;
+      }
+      acc_phase ^= 1u;
+      tc_fence_after();
+
+      float* Y = a.Yout + (long long)b * a.slot_y;
+      const float* Yold = a.Yin + (long long)b * a.slot_y;
+      const long long ld = a.ld_y;
+      __half* ho = a.hi_out ? a.hi_out + (long long)b * a.slot_h : nullptr;
+      __half* lo_ = a.lo_out ? a.lo_out + (long long)b * a.slot_h : nullptr;
+      const long long ldh = a.ld_h;
+      float* D = outD ? a.Dptr[b] : nullptr;
+      double tr = 0.0, sq = 0.0;
+      const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        float v0[32], v1[32];
+        __syncwarp();
+        tmem_ld32(tmem_base + lane_base + ch * 32, v0);
+        if (SPLIT) tmem_ld32(tmem_base + lane_base + BN + ch * 32, v1);
+        tmem_ld_wait();
+        const int c0 = cb0 + ch * 32;
+        float y[32];
+        float sqf = 0.f;
+        if (r < N) {
+          const bool full_chunk = (c0 + 32 <= N) && ((ld & 3) == 0);
+          if (full_chunk) {
+            const float4* src = reinterpret_cast<const float4*>(Yold + (long long)r * ld + c0);
+#pragma unroll
+            for (int j4 = 0; j4 < 8; ++j4) {
+              const float4 o = src[j4];
+              y[4 * j4 + 0] = o.x;
+              y[4 * j4 + 1] = o.y;
+              y[4 * j4 + 2] = o.z;
+              y[4 * j4 + 3] = o.w;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) y[j] = (c0 + j < N) ? Yold[(long long)r * ld + c0 + j] : 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float P = SPLIT ? fmaf(v1[j], a.lo_unscale, v0[j]) : v0[j];
+            float yn = fmaf(p.ca, y[j], p.cb * P);
+            if (r == c0 + j) {
+              yn += p.cc;
+              tr += (double)yn;
+            }
+            if (c0 + j >= N) yn = 0.f;
+            y[j] = yn;
+            sqf = fmaf(yn, yn, sqf);
+          }
+          sq += (double)sqf;
+          if (outD) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int c = c0 + j;
+              if (c < N) {
+                const float d = (r == c) ? y[j] + p.alpha_out : y[j];
+                D[(long long)r * N + c] = d;
+              }
+            }
+          } else {
+            if (full_chunk) {
+              float4* dst = reinterpret_cast<float4*>(Y + (long long)r * ld + c0);
+#pragma unroll
+              for (int j4 = 0; j4 < 8; ++j4)
+                dst[j4] = make_float4(y[4 * j4], y[4 * j4 + 1], y[4 * j4 + 2], y[4 * j4 + 3]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (c0 + j < N) Y[(long long)r * ld + c0 + j] = y[j];
+            }
+            if (ho) {
+              // 32 halves = 64 B per part; the padded row tail [N, ld_h) stays zero
+              __align__(16) __half hh[32], ll[32];
+#pragma unroll
+              for (int j = 0; j < 32; ++j) split_fp16(y[j], a.lo_scale, hh[j], ll[j]);
+              // columns >= N hold y = 0, so the padded row tail [N, ld_h) stays zero
+              if (c0 + 32 <= (int)ldh) {
+                uint4* dh = reinterpret_cast<uint4*>(ho + (long long)r * ldh + c0);
+                const uint4* sh = reinterpret_cast<const uint4*>(hh);
+#pragma unroll
+                for (int j4 = 0; j4 < 4; ++j4) dh[j4] = sh[j4];
+                if (lo_) {
+                  uint4* dl = reinterpret_cast<uint4*>(lo_ + (long long)r * ldh + c0);
+                  const uint4* sl = reinterpret_cast<const uint4*>(ll);
+#pragma unroll
+                  for (int j4 = 0; j4 < 4; ++j4) dl[j4] = sl[j4];
+                }
+              } else {
+                for (int j = 0; j < 32; ++j)
+                  if (c0 + j < (int)ldh) {
+                    ho[(long long)r * ldh + c0 + j] = hh[j];
+                    if (lo_) lo_[(long long)r * ldh + c0 + j] = ll[j];
+                  }
+              }
+            }
+          }
+        }
+        // mirrored store: lanes hold consecutive rows r -> consecutive columns
+        if (mirror) {
+#pragma unroll 4
+          for (int j = 0; j < 32; ++j) {
+            const int c = c0 + j;
+            if (c < N && r < N) {
+              if (outD) {
+                D[(long long)c * N + r] = y[j];
+              } else {
+                Y[(long long)c * ld + r] = y[j];
+                if (ho) {
+                  __half hh, ll;
+                  split_fp16(y[j], a.lo_scale, hh, ll);
+                  ho[(long long)c * ldh + r] = hh;
+                  if (lo_) lo_[(long long)c * ldh + r] = ll;
+                }
+              }
+            }
+          }
+        }
+      }
+      // accumulator drained: let the MMA warp start the next tile
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tmem_empty);
+
+      if (mirror) sq *= 2.0;
+      tr = warp_sum_d(tr);
+      sq = warp_sum_d(sq);
+      if (lane == 0) {
+        s_red[q][0] = tr;
+        s_red[q][1] = sq;
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (warp == 2) {
+        double T = 0.0, Q = 0.0;
+        if (lane == 0)
+          for (int k = 0; k < 4; ++k) {
+            T += s_red[k][0];
+            Q += s_red[k][1];
+          }
+        finish_tile_warp(a, t, b, T, Q);
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
+}  // namespace tc
+
+size_t syrk_tc_smem_bytes(bool split) {
+  const int stages = split ? tc::STAGES_SPLIT : tc::STAGES_PLAIN;
+  const int sb = split ? tc::STAGE_SPLIT : tc::STAGE_PLAIN;
+  return (size_t)stages * sb + 1024 /* alignment slack */ + 256 /* barriers */;
+}
+
+cudaError_t launch_syrk_tc(const SqArgs& a, const CUtensorMap* tm, bool split, int grid, cudaStream_t st) {
+  const size_t smem = syrk_tc_smem_bytes(split);
+  cudaError_t e;
+  if (split) {
+    e = cudaFuncSetAttribute(tc::syrk_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tc::syrk_tc_kernel<true><<<grid, tc::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], a);
+  } else {
+    e = cudaFuncSetAttribute(tc::syrk_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tc::syrk_tc_kernel<false><<<grid, tc::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sp2

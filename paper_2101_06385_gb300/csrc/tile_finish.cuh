@@ -1,0 +1,46 @@
+// Per-tile completion of the squaring kernels: each tile publishes its FP64
+// (tr Y', ||Y'||_F^2) partial; the warp that completes the last tile of an
+// instance sums that instance's partials in tile order (deterministic) and
+// runs the instance's SP2 control step (or stores the traces).
+#pragma once
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sp2 {
+
+// Warp-collective: all 32 lanes of one warp call it; (tr, sq) valid in lane 0.
+__device__ inline void finish_tile_warp(const SqArgs& a, int t, int b, double tr, double sq) {
+  const int lane = threadIdx.x & 31;
+  unsigned last = 0;
+  if (lane == 0) {
+    a.tile_part[t] = make_double2(tr, sq);
+    __threadfence();
+    const unsigned done = atomicAdd(&a.inst_done[b], 1u);
+    last = (done == (unsigned)a.tile_cnt[b] - 1u) ? 1u : 0u;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence();
+  const int off = a.tile_off[b], cnt = a.tile_cnt[b];
+  double T = 0.0, Q = 0.0;
+#pragma unroll 4
+  for (int k = lane; k < cnt; k += 32) {
+    const double2 p = __ldcg(&a.tile_part[off + k]);
+    T += p.x;
+    Q += p.y;
+  }
+  T = warp_sum_d(T);
+  Q = warp_sum_d(Q);
+  if (lane == 0) {
+    a.inst_done[b] = 0u;
+    if (a.ctl)
+      control_step(a.ctl + b, T, Q);
+    else if (a.traces_out) {
+      a.traces_out[2 * b] = T;
+      a.traces_out[2 * b + 1] = Q;
+    }
+  }
+}
+
+}  // namespace sp2
