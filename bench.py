@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of the split-FP16 SP2 solve (Alg. 1 + Eq. 15) on one GB300.
+
+Workload: the large mixed-precision case, N = 16384, N_occ = 8192, spectrum
+U[-2, -0.025] U U[0.025, 2], H = Q diag(eps) Q^T with Q from the QR of a
+seeded Gaussian matrix (seed 0), stored FP32.  One step = one complete solve
+H -> D (Gershgorin bounds, input layer, all squaring layers, refinement).
+
+Printed (one JSON line on rank 0):
+  value      effective TFLOP/s = (squaring layers incl. refinement) x 2 N^3 / time-to-D
+             (2 N^3 = the work of one dense N x N square; same count for every arm)
+  ms_per_step  time-to-D (device time, CUDA events)
+  e2e        the same metric through the C ABI with H copied from pinned host
+             memory and D copied back inside the timed region
+  roofline   the squaring kernel: 3 N^3 algorithmic tensor FLOPs per launch
+             (hi hi + hi lo + lo hi over the upper half) / its mean launch time
+  cpu_baseline  the FP64 oracle on a bounded sample of the same workload
+Also: the plain FP32 (FFMA) path's time-to-D on the same input, and sampled
+parity of D against the closed form Q_occ Q_occ^T.
+
+--impl reference times the FP64 CPU oracle itself (one row block of one
+layer per step) on the same workload and prints the same line with
+"impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(N=16384, n_occ=8192, occ=(-2.0, -0.025), virt=(0.025, 2.0), seed=0)
+METRIC = "SP2 time-to-D and TFLOP/s at N=16384 vs FP32 path, max-abs err vs FP64 oracle"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=WORKLOAD["N"])
+    ap.add_argument("--max-iter", type=int, default=100)
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparator")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU sample")
+    return ap.parse_args()
+
+
+def _workload(n):
+    w = dict(WORKLOAD)
+    if n != w["N"]:
+        w["N"], w["n_occ"] = n, n // 2
+    return w
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return FALLBACK_PEAKS, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="sp2clk", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_from_profile(n):
+    """DRAM bytes per launch of the squaring kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    prof = os.path.join(ROOT, "profiles", "syrk_tc_split_n16384.md")
+    src = os.path.join(ROOT, "paper_2101_06385_gb300", "csrc", "syrk_tc.cu")
+    if not os.path.exists(prof) or n != WORKLOAD["N"]:
+        return None
+    text = open(prof).read()
+    m = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
+    t = re.search(r"dram_bytes_per_launch_n16384:\s*([0-9.eE+]+)", text)
+    if not m or not t:
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return float(t.group(1)) if h == m.group(1) else None
+
+
+def _cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def _oracle_sample(H64, w, target_s):
+    """FP64 oracle on a bounded sample: Gershgorin + input layer, then one
+    layer restricted to a block of rows, sized to take about target_s."""
+    import oracle
+
+    N = w["N"]
+    t0 = time.perf_counter()
+    lo, hi = oracle.gershgorin_bounds(H64)
+    S0 = oracle.input_layer(H64, lo, hi)
+    t_pro = time.perf_counter() - t0
+    rows = 256
+    t0 = time.perf_counter()
+    oracle.sp2_layer_sample(S0, rows)
+    dt = time.perf_counter() - t0
+    rows = int(min(N, max(256, rows * target_s / max(dt, 1e-3))))
+    rows = max(256, rows // 256 * 256)
+    return S0, rows, t_pro
+
+
+def run_reference(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    w = _workload(args.n)
+    import sp2_inputs
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    h = sp2_inputs.gapped_hamiltonian(w["N"], w["n_occ"], w["occ"], w["virt"], w["seed"], device=dev)
+    H64 = h.H.astype(np.float32).astype(np.float64)
+    del h
+    import oracle
+
+    S0, rows, _ = _oracle_sample(H64, w, max(2.0, min(args.cpu_seconds, 20.0)))
+    N = w["N"]
+    for _ in range(args.warmup):
+        oracle.sp2_layer_sample(S0, rows)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sp2_layer_sample(S0, rows)
+    dt = (time.perf_counter() - t0) / args.steps
+    flops = 2.0 * rows * N * N
+    value = flops / dt / 1e12
+    cores = _cpu_threads()
+    sample = f"one SP2 layer (S[:{rows}] @ S, update, trace) of the N={N} workload per step, FP64 numpy"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"sp2_dense_gapped_N{N}_nocc{w['n_occ']}", "N": N, "n_occ": w["n_occ"],
+                   "flop_convention": "2N^3 per squaring layer (dense-square equivalent)",
+                   "l2": "inputs (1 GiB FP32 H) larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    import paper_2101_06385_gb300 as sp2
+    import sp2_inputs
+
+    w = _workload(args.n)
+    N, n_occ = w["N"], w["n_occ"]
+    t_gen = time.perf_counter()
+    h = sp2_inputs.gapped_hamiltonian(N, n_occ, w["occ"], w["virt"], w["seed"], device=str(dev))
+    t_gen = time.perf_counter() - t_gen
+    H32 = h.h32()
+    H = torch.from_numpy(H32).to(dev)
+    D = torch.empty_like(H)
+    sp2.init(dev.index, precision="split")
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        sp2.density_matrix(H, n_occ, max_iter=args.max_iter, out=D, precision="split")
+    clk = Clocks(dev.index if dev.index is not None else 0)
+    barrier()
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    e0.record()
+    for _ in range(args.steps):
+        _, st = sp2.density_matrix(H, n_occ, max_iter=args.max_iter, out=D, precision="split")
+        stats.append(st)
+    e1.record()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    st = stats[-1]
+    layers = st.iterations + 2
+    flops_eff = layers * 2.0 * N ** 3
+    value = flops_eff * ws / (ms * 1e-3) / 1e12
+
+    # squaring kernel: active launches of the timed steps
+    act = [x for s in stats for x in s.layer_ms[: s.iterations + 2]]
+    idle = [x for s in stats for x in s.layer_ms[s.iterations + 2:]]
+    launch_ms = statistics.mean(act)
+    alg_flops = 3.0 * N ** 3
+    peaks, src = _peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    achieved = alg_flops / (launch_ms * 1e-3) / 1e12
+    T = (N + 255) // 256
+    exec_flops = 2.0 * 128 * 256 * 3 * N * (T * (T + 1))  # two 128x256 CTA tiles per upper 256x256 super tile
+    traffic = _traffic_from_profile(N)
+
+    # sampled check of D against the generator's eigenvectors (D_ij = sum over
+    # occupied k of Q_ik Q_jk); the full-size parity test lives in tests/
+    rng = np.random.default_rng(123)
+    ii = rng.integers(0, N, 4096)
+    jj = rng.integers(0, N, 4096)
+    dd = rng.integers(0, N, 256)
+    Dh = D.cpu().numpy()
+    want = np.einsum("ik,ik->i", h.Q[ii, :n_occ], h.Q[jj, :n_occ])
+    want_d = np.einsum("ik,ik->i", h.Q[dd, :n_occ], h.Q[dd, :n_occ])
+    diff = np.concatenate([Dh[ii, jj] - want, Dh[dd, dd] - want_d])
+    ref = np.concatenate([want, want_d])
+    max_abs = float(np.max(np.abs(diff)))
+    rel_frob = float(np.sqrt(np.mean(diff ** 2) / max(np.mean(ref ** 2), 1e-300)))
+    trace_err = abs(float(np.trace(Dh.astype(np.float64))) - n_occ)
+
+    # FP32 (FFMA) comparator on the same input
+    fp32 = None
+    if not args.no_fp32:
+        Df = torch.empty_like(H)
+        sp2.density_matrix(H, n_occ, max_iter=args.max_iter, out=Df, precision="fp32")
+        torch.cuda.synchronize(dev)
+        _, sf = sp2.density_matrix(H, n_occ, max_iter=args.max_iter, out=Df, precision="fp32")
+        Dfh = Df.cpu().numpy()
+        fdiff = np.concatenate([Dfh[ii, jj] - want, Dfh[dd, dd] - want_d])
+        fp32 = {"time_to_D_ms": sf.time_ms, "layers": sf.iterations + 2,
+                "speedup_split_vs_fp32": sf.time_ms / ms,
+                "max_abs_err_sampled": float(np.max(np.abs(fdiff)))}
+        del Df
+        sp2.set_precision("split")
+
+    # end to end through the C ABI: pinned host H -> device -> solve -> host D
+    Hh = torch.from_numpy(H32).pin_memory()
+    Dhost = torch.empty_like(Hh).pin_memory()
+    Hd = torch.empty_like(H)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    s0.record()
+    e2e_layers = 0
+    for _ in range(args.e2e_steps):
+        Hd.copy_(Hh, non_blocking=True)
+        _, se = sp2.density_matrix(Hd, n_occ, max_iter=args.max_iter, out=D, precision="split")
+        Dhost.copy_(D, non_blocking=True)
+        e2e_layers += se.iterations + 2
+    s1.record()
+    barrier()
+    e2e_ms = s0.elapsed_time(s1) / args.e2e_steps
+    e2e_value = (e2e_layers / args.e2e_steps) * 2.0 * N ** 3 * ws / (e2e_ms * 1e-3) / 1e12
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and ws == 1:
+        import oracle
+
+        H64 = H32.astype(np.float64)
+        S0, rows, t_pro = _oracle_sample(H64, w, args.cpu_seconds)
+        t0 = time.perf_counter()
+        oracle.sp2_layer_sample(S0, rows)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 2.0 * rows * N * N / dt / 1e12, "unit": "TFLOP/s", "cores": _cpu_threads(),
+               "kind": "oracle",
+               "sample": f"one FP64 SP2 layer restricted to {rows} of {N} rows (S[:rows] @ S + update + trace), "
+                         f"{dt:.1f} s; full solve would be ~{layers} layers x {N // rows} blocks"}
+        del S0, H64
+
+    launches_per_step = 2 + st.launches
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16",
+        "data": "synthetic (seeded gapped Hamiltonian, dense QR eigenvectors)",
+        "config": {"workload": f"sp2_dense_gapped_N{N}_nocc{n_occ}", "N": N, "n_occ": n_occ,
+                   "spectrum": "U[-2,-0.025] U U[0.025,2]", "seed": w["seed"],
+                   "precision": "split-FP16 (hi + 2^-11 lo) tcgen05 products, FP32 accumulation/storage, "
+                                "FP64 bounds/traces/control, alpha*I shift",
+                   "flop_convention": "value: 2N^3 per squaring layer incl. 2 refinement layers (dense-square "
+                                      "equivalent); roofline: 3N^3 per split layer (upper half)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "no flush: inputs (1 GiB FP32 H, 1.5 GiB iterate + splits) larger than L2",
+                   "time_to_D_ms": ms, "layers": layers, "loop_layers": st.iterations,
+                   "converged_by": st.converged_by, "generator_s": round(t_gen, 1),
+                   "paper_convention_tflops": st.iterations * 4.0 * N ** 3 / (sum(
+                       st.layer_ms[: st.iterations]) * 1e-3) / 1e12},
+        "accuracy": {"max_abs_err_sampled": max_abs, "rel_frob_sampled": rel_frob, "trace_err": trace_err,
+                     "samples": int(len(diff)), "tolerance_max_abs": 5e-5, "tolerance_trace": 1e-4},
+        "fp32_path": fp32,
+        "e2e": {"value": e2e_value, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(N * N * 4), "d2h_bytes_per_step": int(N * N * 4)},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{src} bf16_tflops_sustained (FP16 dense = BF16 dense rate)",
+                     "kernel": "syrk_tc_kernel<split>", "launch_ms_mean": launch_ms,
+                     "idle_launch_ms_mean": statistics.mean(idle) if idle else None,
+                     "executed_tflops": exec_flops / (launch_ms * 1e-3) / 1e12},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "gpu_launches": int(launches_per_step * args.steps),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -89,8 +89,13 @@ typedef struct {
   double alpha;                   /* identity shift of the last iterate (0 without shift) */
   double time_ms;                 /* device time of the whole call (CUDA events) */
   double flops_alg;               /* algorithmic FLOPs: layers x 3N^3 (split), N^3 (fp16/fp32) */
+  double prologue_ms;             /* device time of the bounds + input layer kernels */
+  int launches;                   /* squaring launches enqueued (max_iter + 2); launches past
+                                     iterations + 2 find the solve finished and return at once */
   int8_t sigma[SP2_MAX_LAYERS];   /* sigma[k] = sigma_{k+1} in {+1,-1}; 0 past the end */
   double iderr[SP2_MAX_LAYERS];   /* iderr[k] = IdErr_{k+1} */
+  float layer_ms[SP2_MAX_LAYERS]; /* device time of squaring launch k (k < launches): the loop
+                                     layers, then the two refinement layers of Eq. 15 */
 } sp2_stats;
 
 /* Library set-up.  cfg == NULL selects the defaults {device 0, NULL stream,

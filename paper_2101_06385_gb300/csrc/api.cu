@@ -56,7 +56,7 @@ void set_err(const char* fmt, ...) {
 
 enum BufId {
   B_HI0, B_LO0, B_HI1, B_LO1, B_Y0, B_Y1, B_CTL, B_TILES, B_TOFF, B_TCNT, B_TPART, B_IDONE,
-  B_PART, B_TICKET, B_ERR, B_DPTR, B_NS, B_HS, B_TRACES, B_PARAMS, B_BOUNDS, B_COUNT
+  B_PART, B_TICKET, B_ERR, B_DPTR, B_NS, B_HS, B_TRACES, B_PARAMS, B_BOUNDS, B_RN, B_PART2, B_COUNT
 };
 
 struct Buf {
@@ -80,6 +80,7 @@ struct State {
   size_t stage_bytes = 0;
   cudaEvent_t stage_done = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t lev[SP2_MAX_LAYERS + 1] = {};  // around each squaring launch
   // cached tile list
   int tiles_key_N = -1, tiles_key_B = -1, tiles_key_kind = -1;
 };
@@ -327,6 +328,7 @@ sp2_status sp2_init(const sp2_config* cfg) {
     CK(cudaEventCreateWithFlags(&g.stage_done, cudaEventDisableTiming));
     CK(cudaEventCreate(&g.ev0));
     CK(cudaEventCreate(&g.ev1));
+    for (int i = 0; i <= SP2_MAX_LAYERS; ++i) CK(cudaEventCreate(&g.lev[i]));
   }
   g.device = c.device;
   g.stream = (cudaStream_t)c.stream;
@@ -353,6 +355,10 @@ sp2_status sp2_finalize(void) {
   if (g.ev0) cudaEventDestroy(g.ev0);
   if (g.ev1) cudaEventDestroy(g.ev1);
   g.stage_done = g.ev0 = g.ev1 = nullptr;
+  for (int i = 0; i <= SP2_MAX_LAYERS; ++i) {
+    if (g.lev[i]) cudaEventDestroy(g.lev[i]);
+    g.lev[i] = nullptr;
+  }
   g.tiles_key_N = -1;
   g.init = false;
   return SP2_OK;
@@ -484,6 +490,13 @@ sp2_status sp2_layer(const float* X, int B, int N, float a, float b, float c, fl
   A.lo_scale = std::ldexp(1.0f, g.lo_scale_exp);
   A.lo_unscale = std::ldexp(1.0f, -g.lo_scale_exp);
   A.err = (int*)err;
+  void* rn;
+  CKS(ws(B_RN, (size_t)B * N * sizeof(double), &rn));
+  const int rgrid = (int)std::min<long long>((N + 7) / 8, std::max(1, 2 * g.num_sms / B));
+  CK(launch_rownorm(X, N, (long long)N * N, (const int*)ns, B, N, (double*)rn, N, nullptr, nullptr, nullptr, rgrid,
+                    g.stream));
+  A.rn = (const double*)rn;
+  A.ld_rn = N;
   if (tc) {
     const long long ld_h = round_up(N, 64), slot_h = ld_h * N;
     void *hi, *lo = nullptr;
@@ -542,8 +555,11 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
   CKS(ws(B_ERR, sizeof(int), &err, true));
   const int ggrid = (int)std::min<long long>((N + 7) / 8, 4LL * g.num_sms);
   const int igrid = (int)std::min<long long>(N, 8LL * g.num_sms);
-  CKS(ws(B_PART, std::max(ggrid, igrid) * sizeof(double2), &part));
+  const int rgrid = (int)std::min<long long>((N + 7) / 8, 2LL * g.num_sms);
+  CKS(ws(B_PART, std::max(std::max(ggrid, igrid), rgrid) * sizeof(double2), &part));
   CKS(ws(B_TICKET, 64 * sizeof(unsigned), &tick, true));
+  void* rn;
+  CKS(ws(B_RN, (size_t)N * sizeof(double), &rn));
 
   // small per-call records through pinned staging
   void* h;
@@ -578,6 +594,8 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
   A.lo_scale = std::ldexp(1.0f, g.lo_scale_exp);
   A.lo_unscale = std::ldexp(1.0f, -g.lo_scale_exp);
   A.err = (int*)err;
+  A.rn = (const double*)rn;
+  A.ld_rn = N;
 
   CK(cudaEventRecord(g.ev0, st));
   CK(launch_gershgorin(H, N, N, (long long)N * N, 1, (double2*)part, (unsigned*)tick, (Ctl*)ctl, nullptr, ggrid, st));
@@ -597,6 +615,9 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
     CK(launch_input_layer((const float* const*)hs, (const int*)ns, N, D_out, N, (long long)N * N, (__half*)hi[0],
                           (__half*)lo[0], ld_h, slot_h, N, (int)ld_h, A.lo_scale, (Ctl*)ctl, nullptr, (double2*)part,
                           (unsigned*)tick, g.shift, 1, 1, igrid, st));
+    // FP64 row norms of Y_0 and the first control step (sigma_1, IdErr_1)
+    CK(launch_rownorm(D_out, N, (long long)N * N, (const int*)ns, 1, N, (double*)rn, N, (Ctl*)ctl, (double2*)part,
+                      (unsigned*)tick, rgrid, st));
     CUtensorMap m[2][4];
     CKS(tmaps_for(hi[0], lo[0], N, 1, ld_h, slot_h, m[0]));
     CKS(tmaps_for(hi[1], lo[1], N, 1, ld_h, slot_h, m[1]));
@@ -607,11 +628,15 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
     A.ld_h = ld_h;
     A.slot_h = slot_h;
     const int grid = std::min(ntiles, g.num_sms);
+    CK(cudaEventRecord(g.lev[0], st));
     for (int k = 0; k < max_iter + 2; ++k) {
       const int cur = k & 1;
       A.hi_out = (__half*)hi[cur ^ 1];
       A.lo_out = (__half*)lo[cur ^ 1];
       CK(launch_syrk_tc(A, m[cur], split, grid, st));
+      CK(launch_rownorm(D_out, N, (long long)N * N, (const int*)ns, 1, N, (double*)rn, N, (Ctl*)ctl, (double2*)part,
+                        (unsigned*)tick, rgrid, st));
+      CK(cudaEventRecord(g.lev[k + 1], st));
     }
   } else {
     const long long ld_y = round_up(N, 4), slot_y = ld_y * N;
@@ -621,13 +646,19 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
     CK(launch_input_layer((const float* const*)hs, (const int*)ns, N, (float*)Y[0], ld_y, slot_y, nullptr, nullptr, 0,
                           0, N, N, A.lo_scale, (Ctl*)ctl, nullptr, (double2*)part, (unsigned*)tick, g.shift, 1, 1, igrid,
                           st));
+    CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, 1, N, (double*)rn, N, (Ctl*)ctl, (double2*)part,
+                      (unsigned*)tick, rgrid, st));
     A.ld_y = ld_y;
     A.slot_y = slot_y;
+    CK(cudaEventRecord(g.lev[0], st));
     for (int k = 0; k < max_iter + 2; ++k) {
       const int cur = k & 1;
       A.Yin = (float*)Y[cur];
       A.Yout = (float*)Y[cur ^ 1];
       CK(launch_syrk_simt(A, ntiles, st));
+      CK(launch_rownorm((float*)Y[cur ^ 1], ld_y, slot_y, (const int*)ns, 1, N, (double*)rn, N, (Ctl*)ctl,
+                        (double2*)part, (unsigned*)tick, rgrid, st));
+      CK(cudaEventRecord(g.lev[k + 1], st));
     }
   }
   CK(cudaEventRecord(g.ev1, st));
@@ -643,6 +674,15 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
   const Ctl& c = *(const Ctl*)hb;
   const int e = *(const int*)((char*)hb + sizeof(Ctl));
   fill_stats(c, stats, ms, prec);
+  stats->launches = max_iter + 2;
+  float pm = 0.f;
+  CK(cudaEventElapsedTime(&pm, g.ev0, g.lev[0]));
+  stats->prologue_ms = pm;
+  for (int k = 0; k < max_iter + 2; ++k) {
+    float lm = 0.f;
+    CK(cudaEventElapsedTime(&lm, g.lev[k], g.lev[k + 1]));
+    stats->layer_ms[k] = lm;
+  }
   return status_of(c, e);
 }
 

@@ -47,6 +47,7 @@ struct Ctl {
   int status, sigma_a, pad0, pad1;
   double alpha, alpha_next;   // shift of the stored iterate / of the one being computed
   double trY, sqY;            // tr Y, ||Y||_F^2 of the stored Y
+  double trY_new;             // tr Y of the iterate just written (set by the squaring launch)
   double e_min, e_max;
   double trace_final;
   LayerParams next;           // parameters of the next squaring launch
@@ -144,39 +145,6 @@ __device__ inline void control_step(Ctl* c, double trY, double sqY) {
     c->next.active = 0;
     if (c->status == SP2_OK && c->converged_by == SP2_STOP_MAXITER) c->status = SP2_NOT_CONVERGED;
   }
-}
-
-// Per-launch reduction of FP64 partials with a last-block ticket: every CTA
-// stores its (trY, sqY) partial, the CTA that arrives last sums them in a
-// fixed order (deterministic) and returns true.  No CTA waits on another.
-__device__ inline bool last_block_reduce(double tr, double sq, double2* partials, unsigned* ticket,
-                                         double& tr_out, double& sq_out) {
-  __shared__ bool s_last;
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = make_double2(tr, sq);
-    __threadfence();
-    const unsigned t = atomicAdd(ticket, 1u);
-    s_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!s_last) return false;
-  __threadfence();
-  if (threadIdx.x < 32) {
-    double a = 0.0, b = 0.0;
-    for (unsigned i = threadIdx.x; i < gridDim.x; i += 32) {
-      const double2 p = __ldcg(&partials[i]);
-      a += p.x;
-      b += p.y;
-    }
-    a = warp_sum_d(a);
-    b = warp_sum_d(b);
-    if (threadIdx.x == 0) {
-      tr_out = a;
-      sq_out = b;
-      *ticket = 0u;
-    }
-  }
-  return threadIdx.x == 0;
 }
 
 // Tile descriptor of the squaring kernels: instance b, block row I, block

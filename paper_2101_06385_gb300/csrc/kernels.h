@@ -38,6 +38,8 @@ struct SqArgs {
   double2* tile_part;      // [ntiles] per-tile (tr, sq) partials
   unsigned* inst_done;     // [batch] tile-completion counters (zero between launches)
   double* traces_out;      // [batch][2] when ctl == nullptr, or nullptr
+  const double* rn;        // [batch][ld_rn] FP64 row norms sum_k Y[r][k]^2 = (Y^2)_rr of the input
+  long long ld_rn;
   float lo_scale;          // 2^s
   float lo_unscale;        // 2^-s
   int* err;                // device error word (SP2_ERR_DEVICE_TIMEOUT on a timed-out wait)
@@ -61,6 +63,13 @@ cudaError_t launch_split_pad(const float* X, long long ld_x, long long slot_x, i
                              __half* hi, __half* lo, long long ld_h, long long slot_h, int grid, cudaStream_t st);
 cudaError_t launch_observable(const float* D, const float* A, long long n, double* block_out, int grid,
                               cudaStream_t st);
+
+// rn[b][i] = sum_k Y[b][i][k]^2 in FP64 for every row of every instance.
+// With ctl: instances whose next launch is inactive are skipped, and the
+// last block of an instance runs its control step with (trY_new, sum rn).
+cudaError_t launch_rownorm(const float* Y, long long ld_y, long long slot_y, const int* Ns, int batch, int max_rows,
+                           double* rn, long long ld_rn, Ctl* ctl, double2* partials, unsigned* tickets, int grid_x,
+                           cudaStream_t st);
 
 cudaError_t launch_syrk_simt(const SqArgs& a, int grid, cudaStream_t st);
 

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) input_layer_kernel(const float* const* __
       const float* hrow = H + (long long)r * ld_in;
       float* yrow = Y + (long long)b * slot_y + (long long)r * ld_y;
       __half* hirow = hi ? hi + (long long)b * slot_h + (long long)r * ld_h : nullptr;
-      __half* lorow = hi ? lo + (long long)b * slot_h + (long long)r * ld_h : nullptr;
+      __half* lorow = (hi && lo) ? lo + (long long)b * slot_h + (long long)r * ld_h : nullptr;
       float sqf = 0.f;
       for (int col = threadIdx.x; col < cols; col += blockDim.x) {
         float y = 0.f;
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256) input_layer_kernel(const float* const* __
           __half h16, l16;
           split_fp16(y, lo_scale, h16, l16);
           hirow[col] = h16;
-          lorow[col] = l16;
+          if (lorow) lorow[col] = l16;
         }
       }
       sq += (double)sqf;
@@ -267,8 +267,83 @@ __global__ void __launch_bounds__(256) input_layer_kernel(const float* const* __
   tickets[b] = 0u;
   Ctl* c = ctl + b;
   if (!active) return;
+  // S_0 = alpha_0 I + Y_0; the row-norm launch that follows runs the first
+  // control step (sigma_1, IdErr_1) with the exact ||Y_0||_F^2.
   c->alpha_next = shift ? e_max * inv : 0.0;
-  control_step(c, T, Q);
+  c->trY_new = T;
+  (void)Q;
+}
+
+// ---------------------------------------------------------------- row norms
+// (Y^2)_ii = sum_k Y_ik^2 for symmetric Y, in FP64 on the CUDA cores.  The
+// tensor cores accumulate with truncation, which biases sums of positive
+// terms (the diagonal of a square) by a relative -K*6e-9; the squaring
+// epilogue takes its diagonal from here instead, and the control step gets
+// ||Y||_F^2 = sum_i rn_i without that bias.  One warp per row: FP32 FMA over
+// 32 consecutive elements (round-to-nearest), FP64 across chunks.
+__global__ void __launch_bounds__(256) rownorm_kernel(const float* __restrict__ Y, long long ld_y, long long slot_y,
+                                                      const int* __restrict__ Ns, double* __restrict__ rn,
+                                                      long long ld_rn, Ctl* __restrict__ ctl,
+                                                      double2* __restrict__ partials, unsigned* __restrict__ tickets) {
+  const int b = blockIdx.y;
+  if (ctl && !ctl[b].next.active) return;
+  const int N = Ns[b];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* Yb = Y + (long long)b * slot_y;
+  const bool vec = ((ld_y & 3) == 0) && ((((uintptr_t)Yb) & 15) == 0);
+  double blk = 0.0;
+  for (int i = blockIdx.x * 8 + warp; i < N; i += gridDim.x * 8) {
+    const float* row = Yb + (long long)i * ld_y;
+    double acc = 0.0;
+    if (vec) {
+      const int n4 = N >> 2;
+      const float4* r4 = reinterpret_cast<const float4*>(row);
+      for (int j0 = 0; j0 < n4; j0 += 32 * 8) {
+        float f = 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = j0 + u * 32 + lane;
+          if (j < n4) {
+            const float4 v = __ldcg(r4 + j);
+            f = fmaf(v.x, v.x, f);
+            f = fmaf(v.y, v.y, f);
+            f = fmaf(v.z, v.z, f);
+            f = fmaf(v.w, v.w, f);
+          }
+        }
+        acc += (double)f;
+      }
+      for (int j = (n4 << 2) + lane; j < N; j += 32) acc += (double)row[j] * (double)row[j];
+    } else {
+      for (int j = lane; j < N; j += 32) acc += (double)row[j] * (double)row[j];
+    }
+    acc = warp_sum_d(acc);
+    if (lane == 0) {
+      rn[(long long)b * ld_rn + i] = acc;
+      blk += acc;
+    }
+  }
+  if (!ctl) return;
+  __shared__ double s_p[8];
+  if (lane == 0) s_p[warp] = blk;
+  __syncthreads();
+  __shared__ bool s_last;
+  double2* part = partials + (long long)b * gridDim.x;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += s_p[w];
+    part[blockIdx.x] = make_double2(t, 0.0);
+    __threadfence();
+    s_last = (atomicAdd(&tickets[b], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double Q = 0.0;
+  for (unsigned k = 0; k < gridDim.x; ++k) Q += __ldcg(&part[k]).x;
+  tickets[b] = 0u;
+  Ctl* c = ctl + b;
+  control_step(c, c->trY_new, Q);
 }
 
 // ---------------------------------------------------------------- split
@@ -354,6 +429,15 @@ cudaError_t launch_input_layer(const float* const* Hs, const int* Ns, long long 
   input_layer_kernel<<<grid, 256, 0, st>>>(Hs, Ns, ld_in, Y, ld_y, slot_y, hi, lo, ld_h, slot_h, rows_pad, cols_pad,
                                            lo_scale, ctl,
                                            bounds, partials, tickets, shift, ctl_step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rownorm(const float* Y, long long ld_y, long long slot_y, const int* Ns, int batch, int max_rows,
+                           double* rn, long long ld_rn, Ctl* ctl, double2* partials, unsigned* tickets, int grid_x,
+                           cudaStream_t st) {
+  (void)max_rows;
+  dim3 grid(grid_x, batch);
+  rownorm_kernel<<<grid, 256, 0, st>>>(Y, ld_y, slot_y, Ns, rn, ld_rn, ctl, partials, tickets);
   return cudaGetLastError();
 }
 

@@ -105,10 +105,13 @@ __global__ void __launch_bounds__(256) syrk_simt_kernel(const SqArgs a) {
         const int c = c0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
         if (c >= N) continue;
         const float yold = Y[(long long)r * ld + c];
-        float y = fmaf(p.ca, yold, p.cb * acc[i][j]);
+        float y;
         if (r == c) {
-          y += p.cc;
+          const double pd = a.rn ? a.rn[(long long)b * a.ld_rn + r] : (double)acc[i][j];
+          y = (float)((double)p.ca * (double)yold + (double)p.cb * pd + (double)p.cc);
           tr += (double)y;
+        } else {
+          y = fmaf(p.ca, yold, p.cb * acc[i][j]);
         }
         sqf = fmaf(y, y, sqf);
         if (outD) {
@@ -136,7 +139,7 @@ __global__ void __launch_bounds__(256) syrk_simt_kernel(const SqArgs a) {
           T += s_red[w][0];
           Q += s_red[w][1];
         }
-      finish_tile_warp(a, t, b, T, Q);
+      finish_tile_warp(a, t, b, T, Q, p.out_mode);
     }
     __syncthreads();
   }

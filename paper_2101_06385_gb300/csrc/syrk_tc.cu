@@ -397,10 +397,14 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const float P = SPLIT ? fmaf(v1[j], a.lo_unscale, v0[j]) : v0[j];
-            float yn = fmaf(p.ca, y[j], p.cb * P);
+            float yn;
             if (r == c0 + j) {
-              yn += p.cc;
+              // diagonal of Y^2 from the FP64 row norms (unbiased), update in FP64
+              const double pd = a.rn ? a.rn[(long long)b * a.ld_rn + r] : (double)P;
+              yn = (float)((double)p.ca * (double)y[j] + (double)p.cb * pd + (double)p.cc);
               tr += (double)yn;
+            } else {
+              yn = fmaf(p.ca, y[j], p.cb * P);
             }
             if (c0 + j >= N) yn = 0.f;
             y[j] = yn;
@@ -495,7 +499,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             T += s_red[k][0];
             Q += s_red[k][1];
           }
-        finish_tile_warp(a, t, b, T, Q);
+        finish_tile_warp(a, t, b, T, Q, p.out_mode);
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
     }

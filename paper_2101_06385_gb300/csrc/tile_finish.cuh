@@ -10,7 +10,10 @@
 namespace sp2 {
 
 // Warp-collective: all 32 lanes of one warp call it; (tr, sq) valid in lane 0.
-__device__ inline void finish_tile_warp(const SqArgs& a, int t, int b, double tr, double sq) {
+// With a control block: a final (OUT_D) launch completes the solve here;
+// otherwise tr Y' is left for the row-norm launch, which owns the exact
+// ||Y'||_F^2 and runs the control step.
+__device__ inline void finish_tile_warp(const SqArgs& a, int t, int b, double tr, double sq, int out_mode) {
   const int lane = threadIdx.x & 31;
   unsigned last = 0;
   if (lane == 0) {
@@ -34,9 +37,12 @@ __device__ inline void finish_tile_warp(const SqArgs& a, int t, int b, double tr
   Q = warp_sum_d(Q);
   if (lane == 0) {
     a.inst_done[b] = 0u;
-    if (a.ctl)
-      control_step(a.ctl + b, T, Q);
-    else if (a.traces_out) {
+    if (a.ctl) {
+      if (out_mode == OUT_D)
+        control_step(a.ctl + b, T, Q);
+      else
+        a.ctl[b].trY_new = T;
+    } else if (a.traces_out) {
       a.traces_out[2 * b] = T;
       a.traces_out[2 * b + 1] = Q;
     }

@@ -111,15 +111,42 @@ def gapped_hamiltonian(
     ``n_occ`` eigenvalues are uniform in ``occ``, ``N - n_occ`` uniform in
     ``virt``; with occ[1] < virt[0] the HOMO-LUMO gap is at least
     virt[0] - occ[1] and the zero-temperature density matrix is unique.
+    ``device`` = "cuda" runs the FP64 QR and the assembly through torch on the
+    GPU (same random numbers; used for the large sizes).
     """
     if not (0 <= n_occ <= N):
         raise ValueError("n_occ must be in [0, N]")
     rng = np.random.default_rng(seed)
-    Q = _haar_q(N, rng, device)
+    if device == "cpu":
+        Q = _haar_q(N, rng, device)
+        e_occ = np.sort(rng.uniform(occ[0], occ[1], n_occ))
+        e_virt = np.sort(rng.uniform(virt[0], virt[1], N - n_occ))
+        eps = np.concatenate([e_occ, e_virt])
+        H = _assemble(Q, eps, device)
+        return Hamiltonian(H=H, Q=Q, eps=eps, n_occ=n_occ, seed=seed)
+    import torch
+
+    G = rng.standard_normal((N, N))
     e_occ = np.sort(rng.uniform(occ[0], occ[1], n_occ))
     e_virt = np.sort(rng.uniform(virt[0], virt[1], N - n_occ))
     eps = np.concatenate([e_occ, e_virt])
-    H = _assemble(Q, eps, device)
+    with torch.no_grad():
+        Gt = torch.from_numpy(G).to(device=device, dtype=torch.float64)
+        del G
+        Qt, Rt = torch.linalg.qr(Gt)
+        del Gt
+        d = torch.sign(torch.diagonal(Rt))
+        d[d == 0] = 1.0
+        del Rt
+        Qt.mul_(d[None, :])
+        et = torch.from_numpy(eps).to(device=device, dtype=torch.float64)
+        Ht = (Qt * et[None, :]) @ Qt.T
+        Ht = 0.5 * (Ht + Ht.T)
+        H = Ht.cpu().numpy()
+        del Ht
+        Q = Qt.cpu().numpy()
+        del Qt
+        torch.cuda.empty_cache()
     return Hamiltonian(H=H, Q=Q, eps=eps, n_occ=n_occ, seed=seed)
 
 
