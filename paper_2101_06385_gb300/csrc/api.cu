@@ -238,6 +238,7 @@ void init_ctl(Ctl* c, int N, int n_occ, double tol, int max_iter) {
   c->eps = g.eps;
   c->phase = PHASE_LOOP;
   c->status = SP2_OK;
+  c->next.active = 1;  // lets the first row-norm launch run the first control step
 }
 
 void fill_stats(const Ctl& c, sp2_stats* s, double ms, int precision) {
@@ -462,7 +463,10 @@ sp2_status sp2_layer(const float* X, int B, int N, float a, float b, float c, fl
   memset(hp, 0, sizeof(*hp));
   hp->ca = b;
   hp->cb = a;
-  hp->cc = c;
+  hp->ca_d = b;
+  hp->cb_d = a;
+  hp->cc_d = c;
+  hp->alpha_out = 0.0;
   hp->active = 1;
   hp->out_mode = OUT_Y;
   CK(cudaMemcpyAsync(ns, hn, B * sizeof(int), cudaMemcpyHostToDevice, g.stream));

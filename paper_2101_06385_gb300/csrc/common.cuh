@@ -29,13 +29,26 @@ enum Phase : int { PHASE_LOOP = 0, PHASE_REFINE_A = 1, PHASE_REFINE_B = 2, PHASE
 
 // Coefficients of one squaring launch.  Written either by the host (network
 // and single-layer entry points) or by the device control step (SP2 loop).
+// Off-diagonal elements use the FP32 copies; diagonal elements are updated
+// in FP64 (exact diagonal of Y^2 from the row norms, exact shifts).
 struct LayerParams {
-  float ca, cb, cc;   // Y' = ca Y + cb P + cc I
-  float alpha_out;    // OUT_D: D = Y' + alpha_out I
+  float ca, cb;       // off-diagonal:  Y'_ij = ca Y_ij + cb P_ij
   int active;         // 0: the launch does nothing (converged / finished)
   int out_mode;       // OutMode
-  int pad0, pad1;
+  double ca_d, cb_d;  // diagonal:      Y'_ii = ca_d Y_ii + cb_d P_ii + cc_d
+  double cc_d;
+  double alpha_out;   // OUT_D: D_ii = Y'_ii + alpha_out, D_ij = Y'_ij
 };
+
+// Re-centring of the shift: while the spectrum of S is still clustered the
+// shift alpha follows the cluster (alpha' = alpha^2 or 2 alpha - alpha^2), so
+// Y stays small and FP32 keeps the relative resolution of the HOMO-LUMO gap.
+// Once the average lambda (1 - lambda) = IdErr / N falls below this fraction
+// the iterate is stored around alpha = 1/2 for good.  S - I/2 of a nearly
+// idempotent S squares to nearly I/4, so the off-diagonal sums of Y^2 are
+// near zero and the truncating tensor-core accumulation has no preferred
+// sign there (it would otherwise shrink them and bias the final trace).
+constexpr double kRecenterFrac = 0.01;
 
 // Device-resident state of one SP2 solve (Alg. 1 scalars, FP64).
 struct Ctl {
@@ -44,7 +57,7 @@ struct Ctl {
   double tol, eps;
   // state
   int phase, n, stop_pending, converged_by;
-  int status, sigma_a, pad0, pad1;
+  int status, sigma_a, recentered, pad1;
   double alpha, alpha_next;   // shift of the stored iterate / of the one being computed
   double trY, sqY;            // tr Y, ||Y||_F^2 of the stored Y
   double trY_new;             // tr Y of the iterate just written (set by the squaring launch)
@@ -69,10 +82,11 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // Branch sigma applied to the stored iterate: sets alpha_next and the launch
-// coefficients (see the header comment).
+// coefficients (see the header comment).  After re-centring, the new iterate
+// is stored around alpha = 1/2: the shift difference goes into cc.
 __device__ inline void set_branch(Ctl* c, int sigma, bool final_layer) {
   const double a = c->alpha;
-  double an, ca, cb;
+  double an, ca, cb, cc = 0.0;
   if (sigma > 0) {
     an = a * a;
     ca = 2.0 * a;
@@ -82,15 +96,20 @@ __device__ inline void set_branch(Ctl* c, int sigma, bool final_layer) {
     ca = 2.0 - 2.0 * a;
     cb = -1.0;
   }
+  if (c->recentered) {
+    cc = an - 0.5;
+    an = 0.5;
+  }
   c->alpha_next = an;
   LayerParams p;
   p.ca = (float)ca;
   p.cb = (float)cb;
-  p.cc = 0.f;
-  p.alpha_out = final_layer ? (float)an : 0.f;
+  p.ca_d = ca;
+  p.cb_d = cb;
+  p.cc_d = cc;
+  p.alpha_out = final_layer ? an : 0.0;
   p.active = 1;
   p.out_mode = final_layer ? OUT_D : OUT_Y;
-  p.pad0 = p.pad1 = 0;
   c->next = p;
 }
 
@@ -123,6 +142,7 @@ __device__ inline void control_step(Ctl* c, double trY, double sqY) {
     const int s = (v >= 0.0) ? 1 : -1;
     c->sigma[n1] = s;
     c->iderr[n1] = err;
+    if (c->shift && !c->recentered && err <= kRecenterFrac * N) c->recentered = 1;
     int stop = SP2_STOP_NONE;
     if (c->tol > 0.0 && err <= c->tol)
       stop = SP2_STOP_TOL;

@@ -105,17 +105,19 @@ __global__ void __launch_bounds__(256) syrk_simt_kernel(const SqArgs a) {
         const int c = c0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
         if (c >= N) continue;
         const float yold = Y[(long long)r * ld + c];
-        float y;
+        float y, d;
         if (r == c) {
           const double pd = a.rn ? a.rn[(long long)b * a.ld_rn + r] : (double)acc[i][j];
-          y = (float)((double)p.ca * (double)yold + (double)p.cb * pd + (double)p.cc);
-          tr += (double)y;
+          const double yd = p.ca_d * (double)yold + p.cb_d * pd + p.cc_d;
+          tr += yd;
+          y = (float)yd;
+          d = (float)(yd + p.alpha_out);
         } else {
           y = fmaf(p.ca, yold, p.cb * acc[i][j]);
+          d = y;
         }
         sqf = fmaf(y, y, sqf);
         if (outD) {
-          const float d = (r == c) ? y + p.alpha_out : y;
           D[(long long)r * N + c] = d;
           if (mirror) D[(long long)c * N + r] = d;
         } else {

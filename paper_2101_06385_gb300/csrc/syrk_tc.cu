@@ -378,6 +378,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int c0 = cb0 + ch * 32;
         float y[32];
         float sqf = 0.f;
+        float ydiag = 0.f;
         if (r < N) {
           const bool full_chunk = (c0 + 32 <= N) && ((ld & 3) == 0);
           if (full_chunk) {
@@ -401,8 +402,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (r == c0 + j) {
               // diagonal of Y^2 from the FP64 row norms (unbiased), update in FP64
               const double pd = a.rn ? a.rn[(long long)b * a.ld_rn + r] : (double)P;
-              yn = (float)((double)p.ca * (double)y[j] + (double)p.cb * pd + (double)p.cc);
-              tr += (double)yn;
+              const double yd = p.ca_d * (double)y[j] + p.cb_d * pd + p.cc_d;
+              tr += yd;
+              yn = (float)yd;
+              if (outD) ydiag = (float)(yd + p.alpha_out);
             } else {
               yn = fmaf(p.ca, y[j], p.cb * P);
             }
@@ -415,10 +418,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const int c = c0 + j;
-              if (c < N) {
-                const float d = (r == c) ? y[j] + p.alpha_out : y[j];
-                D[(long long)r * N + c] = d;
-              }
+              if (c < N) D[(long long)r * N + c] = (r == c) ? ydiag : y[j];
             }
           } else {
             if (full_chunk) {
