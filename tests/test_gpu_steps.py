@@ -107,6 +107,25 @@ def test_layer_is_symmetric_and_mirrored(sp2):
     assert np.max(np.abs(out - out.T)) <= 1e-6 * np.max(np.abs(out))
 
 
+def test_accumulation_bias(sp2):
+    """All-positive square: the tensor-core off-diagonal sums come out biased
+    low (truncating accumulation), the FFMA path does not; the diagonal, taken
+    from FP64 row norms, is unbiased in every precision."""
+    N = 2048
+    rng = np.random.default_rng(0)
+    X = (rng.uniform(0.5, 1.0, (N, N)) / N).astype(np.float32)
+    X = ((X + X.T) / 2).astype(np.float32)
+    exact = X.astype(np.float64) @ X.astype(np.float64)
+    off = ~np.eye(N, dtype=bool)
+    for prec in ("split", "fp32"):
+        out, _ = sp2.layer(_cuda(X), 1.0, 0.0, 0.0, precision=prec)
+        rel = (out.cpu().numpy().astype(np.float64) - exact) / exact
+        print(f"{prec}: mean rel err off-diagonal {rel[off].mean():.3e}, diagonal {np.diag(rel).mean():.3e}")
+        assert abs(np.diag(rel).mean()) < 1e-7
+        if prec == "fp32":
+            assert abs(rel[off].mean()) < 1e-7
+
+
 # ------------------------------------------------------------------ observable
 def test_observable(sp2):
     rng = np.random.default_rng(8)
