@@ -194,6 +194,35 @@ sp2_status sp2_layer(const float* X, int B, int N, float a, float b, float c, fl
  * energy).  D, A [N, N] device; out: HOST double.  Synchronises. */
 sp2_status sp2_observable(const float* D, const float* A, int N, double* out);
 
+/* ---- allocation-free variant (no counterpart in the paper) ---- */
+
+#define SP2_NOALLOC_MAX_N 1024
+#define SP2_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u + 65536u)
+
+/*
+ * sp2_density_matrix for callers that cannot allocate device memory when they
+ * need D: code that runs while a stream is being captured into a CUDA graph,
+ * engines that pre-size every buffer and must not grow the process footprint
+ * mid-run, hosts that hand the library only memory they manage themselves.
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch is
+ * one file-scope device array of SP2_NOALLOC_SCRATCH_BYTES (about 8 MiB),
+ * which every GPU that loads the library holds until the process exits.
+ *
+ *   H, N, N_occ, tol, max_iter, D_out, stats: as sp2_density_matrix, with
+ *            N <= SP2_NOALLOC_MAX_N; larger N returns SP2_ERR_INVALID_ARG
+ *            ("N exceeds SP2_NOALLOC_MAX_N" in sp2_last_error()).
+ *   stream   cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Split-FP16 precision with the sp2_init defaults (shift on, epsilon 0,
+ * low-part scale 2^11); needs no sp2_init.  stats->time_ms and layer_ms are
+ * not measured (0).  The first call on a device, with that device current,
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the array and leave their
+ * contents in it (the zero-start counters are cleared at the start of each
+ * call); calls whose GPU work overlaps (other streams or host threads) race.
+ */
+sp2_status sp2_density_matrix_noalloc(const float* H, int N, int N_occ, double tol, int max_iter,
+                                      float* D_out, sp2_stats* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

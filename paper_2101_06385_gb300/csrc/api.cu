@@ -197,6 +197,8 @@ sp2_status upload_tiles(int N, int B, bool tc, int* ntiles_out) {
 }  // namespace
 
 namespace sp2 {
+void set_error_text(const char* s) { t_err = s; }
+
 bool make_tmap_f16(CUtensorMap* out, const void* base, int cols, int rows, int batch, long long ld, long long slot,
                    int box_k, int box_rows) {
   if (!g.encode) return false;

@@ -1,0 +1,57 @@
+"""The allocation-free entry point (for callers that cannot allocate device
+memory, e.g. inside stream capture or under a fixed memory budget) gives the
+same density matrix as sp2_density_matrix, call after call, through the C ABI."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle as o
+import sp2_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def libs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2101_06385_gb300 as sp2
+
+    sp2.init(0)
+    lib = ctypes.CDLL(sp2.library_path())
+    fn = lib.sp2_density_matrix_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                   ctypes.c_void_p, ctypes.c_void_p]
+    lib.sp2_last_error.restype = ctypes.c_char_p
+    return sp2, lib, fn
+
+
+def test_noalloc_matches_density_matrix_on_consecutive_calls(libs):
+    sp2, lib, fn = libs
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    # two calls in a row; the second one finds the first one's data in the scratch
+    for N, n_occ, seed in [(1000, 400, 21), (512, 256, 22), (1000, 400, 21)]:
+        h = si.gapped_hamiltonian(N, n_occ, (-1.0, -0.1), (0.1, 1.0), seed=seed)
+        H = torch.from_numpy(h.h32()).cuda()
+        D_ref, st_ref = sp2.density_matrix(H, n_occ, precision="split")
+        D = torch.full_like(H, float("nan"))
+        st = sp2._Stats()
+        status = fn(H.data_ptr(), N, n_occ, 0.0, 100, D.data_ptr(), ctypes.byref(st), stream)
+        assert status == 0, lib.sp2_last_error()
+        Dn = D.cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(Dn - D_ref.cpu().numpy())) <= 5e-5
+        m = o.error_metrics(Dn, o.density_matrix_closed_form(h.Q, n_occ), n_occ)
+        assert m["max_abs"] <= 5e-5 and m["trace_err"] <= 1e-4, m
+        assert st.iterations == st_ref.iterations
+
+
+def test_noalloc_rejects_sizes_beyond_its_maximum(libs):
+    sp2, lib, fn = libs
+    H = torch.zeros(1025, 1025, device="cuda")
+    D = torch.empty_like(H)
+    status = fn(H.data_ptr(), 1025, 10, 0.0, 100, D.data_ptr(), None, None)
+    assert status == -1
+    assert b"SP2_NOALLOC_MAX_N" in lib.sp2_last_error()
