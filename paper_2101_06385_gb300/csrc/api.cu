@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -56,7 +57,8 @@ void set_err(const char* fmt, ...) {
 
 enum BufId {
   B_HI0, B_LO0, B_HI1, B_LO1, B_Y0, B_Y1, B_CTL, B_TILES, B_TOFF, B_TCNT, B_TPART, B_IDONE,
-  B_PART, B_TICKET, B_ERR, B_DPTR, B_NS, B_HS, B_TRACES, B_PARAMS, B_BOUNDS, B_RN, B_PART2, B_COUNT
+  B_PART, B_TICKET, B_ERR, B_DPTR, B_NS, B_HS, B_TRACES, B_PARAMS, B_BOUNDS, B_RN, B_PART2,
+  B_G, B_SEG, B_GH0, B_GL0, B_GH1, B_GL1, B_DOTS, B_TDOTS, B_PARAMS2, B_NALPHA, B_COUNT
 };
 
 struct Buf {
@@ -694,23 +696,586 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
 
 sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const int* N_occ, int batch, double tol,
                                       int max_iter, float* const* D_out, sp2_stats* stats) {
-  (void)H; (void)N; (void)N_occ; (void)batch; (void)tol; (void)max_iter; (void)D_out; (void)stats;
-  set_err("sp2_density_matrix_batched: not available in this build");
-  return SP2_ERR_UNSUPPORTED;
+  t_err.clear();
+  CKS(require_init());
+  if (!H || !N || !N_occ || !D_out || batch < 1 || batch > 4096 || !(tol >= 0.0) || !std::isfinite(tol) ||
+      max_iter < 1 || max_iter > SP2_MAX_LAYERS - 3) {
+    set_err("sp2_density_matrix_batched: invalid argument");
+    return SP2_ERR_INVALID_ARG;
+  }
+  int Nmax = 0;
+  for (int i = 0; i < batch; ++i) {
+    if (!H[i] || !D_out[i] || H[i] == D_out[i] || N[i] < 1 || N[i] > 4096 || N_occ[i] < 0 || N_occ[i] > N[i]) {
+      set_err("sp2_density_matrix_batched: invalid argument for instance %d", i);
+      return SP2_ERR_INVALID_ARG;
+    }
+    Nmax = std::max(Nmax, N[i]);
+  }
+  const int prec = g.precision;
+  const bool tc = tc_precision(prec);
+  const bool split = prec == SP2_PREC_SPLIT_FP16;
+  cudaStream_t st = g.stream;
+  const int B = batch;
+
+  // Tile list: instances by decreasing size (largest work first), the tiles
+  // of one instance contiguous (its control step sums them in order).
+  std::vector<int> order(B);
+  for (int i = 0; i < B; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return N[x] > N[y]; });
+  std::vector<uint32_t> tiles;
+  std::vector<int> toff(B), tcnt(B);
+  const int tile = tc ? kTcBN : kSimtB;
+  for (int b : order) {
+    std::vector<uint32_t> one;
+    int per = 0;
+    build_tiles(N[b], 1, tile, tc, one, per);
+    toff[b] = (int)tiles.size();
+    tcnt[b] = per;
+    for (uint32_t t : one) tiles.push_back(t | ((uint32_t)b << 20));
+  }
+  const int nt = (int)tiles.size();
+  g.tiles_key_N = -1;  // the single-size cache no longer matches the device list
+
+  void *dt, *doff, *dcnt, *dpart, *ddone, *ctl, *ns, *hs, *dptr, *err, *part, *tick, *rn;
+  CKS(ws(B_TILES, nt * sizeof(uint32_t), &dt));
+  CKS(ws(B_TOFF, B * sizeof(int), &doff));
+  CKS(ws(B_TCNT, B * sizeof(int), &dcnt));
+  CKS(ws(B_TPART, nt * sizeof(double2), &dpart));
+  CKS(ws(B_IDONE, B * sizeof(unsigned), &ddone, true));
+  CKS(ws(B_CTL, B * sizeof(Ctl), &ctl));
+  CKS(ws(B_NS, B * sizeof(int), &ns));
+  CKS(ws(B_HS, B * sizeof(float*), &hs));
+  CKS(ws(B_DPTR, B * sizeof(float*), &dptr));
+  CKS(ws(B_ERR, sizeof(int), &err, true));
+  const int igrid = (int)std::min<long long>(Nmax, std::max(1, 8 * g.num_sms / B + 1));
+  const int rgrid = (int)std::min<long long>((Nmax + 7) / 8, std::max(1, 2 * g.num_sms / B + 1));
+  CKS(ws(B_PART, (size_t)B * std::max(igrid, rgrid) * sizeof(double2), &part));
+  CKS(ws(B_TICKET, std::max(64, B) * sizeof(unsigned), &tick, true));
+  CKS(ws(B_RN, (size_t)B * Nmax * sizeof(double), &rn));
+
+  // per-call records through pinned staging
+  const size_t bytes = (size_t)B * sizeof(Ctl) + nt * sizeof(uint32_t) + 2 * B * sizeof(int) + B * sizeof(int) +
+                       2 * B * sizeof(void*) + 64;
+  void* h;
+  CKS(staging(bytes, &h));
+  uint8_t* hp = (uint8_t*)h;
+  Ctl* hc = (Ctl*)hp;
+  for (int b = 0; b < B; ++b) init_ctl(hc + b, N[b], N_occ[b], tol, max_iter);
+  const void** hh = (const void**)(hc + B);
+  void** hd = (void**)(hh + B);
+  uint32_t* ht = (uint32_t*)(hd + B);
+  int* hoff = (int*)(ht + nt);
+  int* hcnt = hoff + B;
+  int* hn = hcnt + B;
+  for (int b = 0; b < B; ++b) {
+    hh[b] = H[b];
+    hd[b] = D_out[b];
+    hoff[b] = toff[b];
+    hcnt[b] = tcnt[b];
+    hn[b] = N[b];
+  }
+  memcpy(ht, tiles.data(), nt * sizeof(uint32_t));
+  CK(cudaMemcpyAsync(ctl, hc, B * sizeof(Ctl), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(hs, hh, B * sizeof(void*), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dptr, hd, B * sizeof(void*), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dt, ht, nt * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(doff, hoff, B * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dcnt, hcnt, B * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ns, hn, B * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(g.stage_done, st));
+
+  SqArgs A;
+  memset(&A, 0, sizeof(A));
+  A.Dptr = (float* const*)dptr;
+  A.Ns = (const int*)ns;
+  A.tiles = (const uint32_t*)dt;
+  A.ntiles = nt;
+  A.tile_off = (const int*)doff;
+  A.tile_cnt = (const int*)dcnt;
+  A.ctl = (Ctl*)ctl;
+  A.tile_part = (double2*)dpart;
+  A.inst_done = (unsigned*)ddone;
+  A.rn = (const double*)rn;
+  A.ld_rn = Nmax;
+  A.lo_scale = std::ldexp(1.0f, g.lo_scale_exp);
+  A.lo_unscale = std::ldexp(1.0f, -g.lo_scale_exp);
+  A.err = (int*)err;
+
+  CK(cudaEventRecord(g.ev0, st));
+  CK(launch_gershgorin_batched((const float* const*)hs, (const int*)ns, (Ctl*)ctl, B, st));
+  // iterate Y in uniform slots [B][Nmax][ld_y]; D_out[b] is written by the last layer
+  const long long ld_y = round_up(Nmax, 4), slot_y = ld_y * Nmax;
+  void* Y[2] = {nullptr, nullptr};
+  CKS(ws(B_Y0, (size_t)slot_y * B * 4, &Y[0]));
+  if (tc) {
+    const long long ld_h = round_up(Nmax, 64), slot_h = ld_h * Nmax;
+    void *hi[2], *lo[2] = {nullptr, nullptr};
+    CKS(ws(B_HI0, (size_t)slot_h * B * 2, &hi[0]));
+    CKS(ws(B_HI1, (size_t)slot_h * B * 2, &hi[1]));
+    if (split) {
+      CKS(ws(B_LO0, (size_t)slot_h * B * 2, &lo[0]));
+      CKS(ws(B_LO1, (size_t)slot_h * B * 2, &lo[1]));
+    }
+    // Slots are Nmax x Nmax in the tensor maps: everything outside instance b's
+    // N_b x N_b block must read as zero.  The input layer zero-fills buffer 0's
+    // slot; the epilogues never write outside N_b x N_b (row tails up to the
+    // 32-column chunk are written as zeros), so buffer 1 is cleared here.
+    CK(cudaMemsetAsync(hi[1], 0, (size_t)slot_h * B * 2, st));
+    if (split) CK(cudaMemsetAsync(lo[1], 0, (size_t)slot_h * B * 2, st));
+    CK(launch_input_layer((const float* const*)hs, (const int*)ns, 0, (float*)Y[0], ld_y, slot_y, (__half*)hi[0],
+                          (__half*)lo[0], ld_h, slot_h, Nmax, (int)ld_h, A.lo_scale, (Ctl*)ctl, nullptr,
+                          (double2*)part, (unsigned*)tick, g.shift, 1, B, igrid, st));
+    CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
+                      (double2*)part, (unsigned*)tick, rgrid, st));
+    CUtensorMap m[2][4];
+    CKS(tmaps_for(hi[0], lo[0], Nmax, B, ld_h, slot_h, m[0]));
+    CKS(tmaps_for(hi[1], lo[1], Nmax, B, ld_h, slot_h, m[1]));
+    A.Yin = (float*)Y[0];
+    A.Yout = (float*)Y[0];
+    A.ld_y = ld_y;
+    A.slot_y = slot_y;
+    A.ld_h = ld_h;
+    A.slot_h = slot_h;
+    const int grid = std::min(nt, g.num_sms);
+    CK(cudaEventRecord(g.lev[0], st));
+    for (int k = 0; k < max_iter + 2; ++k) {
+      const int cur = k & 1;
+      A.hi_out = (__half*)hi[cur ^ 1];
+      A.lo_out = (__half*)lo[cur ^ 1];
+      CK(launch_syrk_tc(A, m[cur], split, grid, st));
+      CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
+                        (double2*)part, (unsigned*)tick, rgrid, st));
+      CK(cudaEventRecord(g.lev[k + 1], st));
+    }
+  } else {
+    CKS(ws(B_Y1, (size_t)slot_y * B * 4, &Y[1]));
+    CK(launch_input_layer((const float* const*)hs, (const int*)ns, 0, (float*)Y[0], ld_y, slot_y, nullptr, nullptr, 0,
+                          0, Nmax, Nmax, A.lo_scale, (Ctl*)ctl, nullptr, (double2*)part, (unsigned*)tick, g.shift, 1,
+                          B, igrid, st));
+    CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
+                      (double2*)part, (unsigned*)tick, rgrid, st));
+    A.ld_y = ld_y;
+    A.slot_y = slot_y;
+    CK(cudaEventRecord(g.lev[0], st));
+    for (int k = 0; k < max_iter + 2; ++k) {
+      const int cur = k & 1;
+      A.Yin = (float*)Y[cur];
+      A.Yout = (float*)Y[cur ^ 1];
+      CK(launch_syrk_simt(A, std::min(nt, 65535), st));
+      CK(launch_rownorm((float*)Y[cur ^ 1], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
+                        (double2*)part, (unsigned*)tick, rgrid, st));
+      CK(cudaEventRecord(g.lev[k + 1], st));
+    }
+  }
+  CK(cudaEventRecord(g.ev1, st));
+  if (!stats) return SP2_OK;
+
+  void* hb;
+  CKS(staging((size_t)B * sizeof(Ctl) + 16, &hb));
+  CK(cudaMemcpyAsync(hb, ctl, (size_t)B * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync((char*)hb + (size_t)B * sizeof(Ctl), err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, g.ev0, g.ev1));
+  const Ctl* cs = (const Ctl*)hb;
+  const int e = *(const int*)((char*)hb + (size_t)B * sizeof(Ctl));
+  sp2_status worst = SP2_OK;
+  for (int b = 0; b < B; ++b) {
+    fill_stats(cs[b], &stats[b], ms, prec);
+    stats[b].launches = max_iter + 2;
+    const sp2_status sb = status_of(cs[b], e);
+    if (sb < 0 && worst >= 0) worst = sb;
+    if (sb == SP2_NOT_CONVERGED && worst == SP2_OK) worst = SP2_NOT_CONVERGED;
+  }
+  if (worst == SP2_OK) t_err.clear();
+  return worst;
 }
+
+// Host-side FP64 shift sequence of the network: X_n = alpha_n I + Y_n with
+// alpha_0 = e_max/(e_max - e_min) (shift on) and alpha_{n+1} = a alpha^2 +
+// b alpha + c; the layer on Y is Y' = (2 a alpha + b) Y + a Y^2.
+namespace {
+struct NetPlan {
+  std::vector<double> alpha;       // [(L+1) * B]
+  std::vector<LayerParams> params; // [L * B]
+};
+
+sp2_status network_prologue(const float* H, int B, int N, int L, const float* coef, bool* ok, NetPlan& plan,
+                            void** ctl_out, void** ns_out, void** hs_out, void** dptr_out, float* X_out) {
+  void *ctl, *ns, *hs, *dptr;
+  CKS(ws(B_CTL, (size_t)B * sizeof(Ctl), &ctl));
+  CKS(ws(B_NS, B * sizeof(int), &ns));
+  CKS(ws(B_HS, B * sizeof(float*), &hs));
+  CKS(ws(B_DPTR, B * sizeof(float*), &dptr));
+  void* h;
+  CKS(staging((size_t)B * sizeof(Ctl) + B * (sizeof(int) + 2 * sizeof(void*)) + 64, &h));
+  Ctl* hc = (Ctl*)h;
+  for (int b = 0; b < B; ++b) init_ctl(hc + b, N, N / 2, 0.0, 1);
+  int* hn = (int*)(hc + B);
+  const float** hh = (const float**)(hn + B + (B & 1));
+  float** hd = (float**)(hh + B);
+  for (int b = 0; b < B; ++b) {
+    hn[b] = N;
+    hh[b] = H + (size_t)b * N * N;
+    hd[b] = X_out + (size_t)b * N * N;
+  }
+  CK(cudaMemcpyAsync(ctl, hc, (size_t)B * sizeof(Ctl), cudaMemcpyHostToDevice, g.stream));
+  CK(cudaMemcpyAsync(ns, hn, B * sizeof(int), cudaMemcpyHostToDevice, g.stream));
+  CK(cudaMemcpyAsync(hs, hh, B * sizeof(void*), cudaMemcpyHostToDevice, g.stream));
+  CK(cudaMemcpyAsync(dptr, hd, B * sizeof(void*), cudaMemcpyHostToDevice, g.stream));
+  CK(cudaEventRecord(g.stage_done, g.stream));
+  CK(launch_gershgorin_batched((const float* const*)hs, (const int*)ns, (Ctl*)ctl, B, g.stream));
+  // bounds to the host: the FP64 shift sequence is planned there
+  void* hb;
+  CKS(staging((size_t)B * 2 * sizeof(double) + (size_t)B * sizeof(int), &hb));
+  CK(cudaMemcpy2DAsync(hb, 2 * sizeof(double), (char*)ctl + offsetof(Ctl, e_min), sizeof(Ctl), 2 * sizeof(double),
+                       B, cudaMemcpyDeviceToHost, g.stream));
+  CK(cudaMemcpy2DAsync((char*)hb + (size_t)B * 2 * sizeof(double), sizeof(int), (char*)ctl + offsetof(Ctl, status),
+                       sizeof(Ctl), sizeof(int), B, cudaMemcpyDeviceToHost, g.stream));
+  CK(cudaStreamSynchronize(g.stream));
+  const double* bd = (const double*)hb;
+  const int* bs = (const int*)((char*)hb + (size_t)B * 2 * sizeof(double));
+  plan.alpha.assign((size_t)(L + 1) * B, 0.0);
+  plan.params.assign((size_t)L * B, LayerParams());
+  *ok = true;
+  for (int b = 0; b < B; ++b) {
+    if (bs[b] < 0) {
+      set_err("instance %d: %s", b, bs[b] == SP2_ERR_NONFINITE ? "non-finite spectral bounds" : "degenerate spectrum");
+      *ok = false;
+      return (sp2_status)bs[b];
+    }
+    const double lo = bd[2 * b], hi = bd[2 * b + 1];
+    double a = g.shift ? hi / (hi - lo) : 0.0;
+    plan.alpha[b] = a;
+    for (int n = 0; n < L; ++n) {
+      const double ca = coef[3 * n], cb = coef[3 * n + 1], cc = coef[3 * n + 2];
+      LayerParams p;
+      memset(&p, 0, sizeof(p));
+      p.ca_d = 2.0 * ca * a + cb;  // Y' = (2 a alpha + b) Y + a Y^2
+      p.cb_d = ca;
+      p.cc_d = g.shift ? 0.0 : cc;
+      p.ca = (float)p.ca_d;
+      p.cb = (float)p.cb_d;
+      p.active = 1;
+      const double an = g.shift ? ca * a * a + cb * a + cc : 0.0;
+      p.out_mode = (n == L - 1) ? OUT_D : OUT_Y;
+      p.alpha_out = (n == L - 1) ? an : 0.0;
+      plan.params[(size_t)n * B + b] = p;
+      a = an;
+      plan.alpha[(size_t)(n + 1) * B + b] = a;
+    }
+  }
+  *ctl_out = ctl;
+  *ns_out = ns;
+  *hs_out = hs;
+  *dptr_out = dptr;
+  return SP2_OK;
+}
+}  // namespace
 
 sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float* coef, int ckpt_every, float* X_out,
                                float* ckpt, double* bounds) {
-  (void)H; (void)B; (void)N; (void)L; (void)coef; (void)ckpt_every; (void)X_out; (void)ckpt; (void)bounds;
-  set_err("sp2_network_forward: not available in this build");
-  return SP2_ERR_UNSUPPORTED;
+  t_err.clear();
+  CKS(require_init());
+  if (!H || !X_out || !coef || H == X_out || B < 1 || B > 4096 || N < 1 || N > 8192 ||
+      (long long)B * N * N >= (1LL << 31) || L < 1 || L > 256 || ckpt_every < 1 || ckpt_every > L) {
+    set_err("sp2_network_forward: invalid argument");
+    return SP2_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < 3 * L; ++i)
+    if (!std::isfinite(coef[i])) {
+      set_err("sp2_network_forward: non-finite coefficient");
+      return SP2_ERR_INVALID_ARG;
+    }
+  const bool tc = tc_precision(g.precision);
+  const bool split = g.precision == SP2_PREC_SPLIT_FP16;
+  cudaStream_t st = g.stream;
+  bool ok = false;
+  NetPlan plan;
+  void *ctl, *ns, *hs, *dptr;
+  CKS(network_prologue(H, B, N, L, coef, &ok, plan, &ctl, &ns, &hs, &dptr, X_out));
+  if (bounds)
+    CK(cudaMemcpy2DAsync(bounds, 2 * sizeof(double), (char*)ctl + offsetof(Ctl, e_min), sizeof(Ctl),
+                         2 * sizeof(double), B, cudaMemcpyDeviceToDevice, st));
+  int ntiles = 0;
+  CKS(upload_tiles(N, B, tc, &ntiles));
+  void *params, *alpha, *rn, *part, *tick, *err;
+  CKS(ws(B_PARAMS, plan.params.size() * sizeof(LayerParams), &params));
+  CKS(ws(B_BOUNDS, plan.alpha.size() * sizeof(double), &alpha));
+  CKS(ws(B_RN, (size_t)B * N * sizeof(double), &rn));
+  const int igrid = (int)std::min<long long>(N, std::max(1, 8 * g.num_sms / B + 1));
+  CKS(ws(B_PART, (size_t)B * igrid * sizeof(double2), &part));
+  CKS(ws(B_TICKET, std::max(64, B) * sizeof(unsigned), &tick, true));
+  CKS(ws(B_ERR, sizeof(int), &err, true));
+  void* h;
+  CKS(staging(plan.params.size() * sizeof(LayerParams) + plan.alpha.size() * sizeof(double), &h));
+  memcpy(h, plan.params.data(), plan.params.size() * sizeof(LayerParams));
+  memcpy((char*)h + plan.params.size() * sizeof(LayerParams), plan.alpha.data(), plan.alpha.size() * sizeof(double));
+  CK(cudaMemcpyAsync(params, h, plan.params.size() * sizeof(LayerParams), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(alpha, (char*)h + plan.params.size() * sizeof(LayerParams), plan.alpha.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(g.stage_done, st));
+
+  const long long slot = (long long)N * N;
+  SqArgs A;
+  memset(&A, 0, sizeof(A));
+  A.Dptr = (float* const*)dptr;
+  A.Ns = (const int*)ns;
+  A.tiles = (const uint32_t*)g.buf[B_TILES].p;
+  A.ntiles = ntiles;
+  A.tile_off = (const int*)g.buf[B_TOFF].p;
+  A.tile_cnt = (const int*)g.buf[B_TCNT].p;
+  A.ctl = nullptr;
+  A.lp_per_instance = 1;
+  A.tile_part = (double2*)g.buf[B_TPART].p;
+  A.inst_done = (unsigned*)g.buf[B_IDONE].p;
+  A.traces_out = nullptr;
+  A.rn = (const double*)rn;
+  A.ld_rn = N;
+  A.lo_scale = std::ldexp(1.0f, g.lo_scale_exp);
+  A.lo_unscale = std::ldexp(1.0f, -g.lo_scale_exp);
+  A.err = (int*)err;
+  A.ld_y = N;
+  A.slot_y = slot;
+  const int mgrid = (int)std::min<long long>(N, std::max(1, 4 * g.num_sms / B + 1));
+  const int rgrid = (int)std::min<long long>((N + 7) / 8, std::max(1, 2 * g.num_sms / B + 1));
+  auto ckpt_slot = [&](int k) { return ckpt + (size_t)k * B * slot; };
+
+  void* Y[2] = {X_out, nullptr};
+  void *hi[2] = {nullptr, nullptr}, *lo[2] = {nullptr, nullptr};
+  long long ld_h = 0, slot_h = 0;
+  CUtensorMap m[2][4];
+  if (tc) {
+    ld_h = round_up(N, 64);
+    slot_h = ld_h * N;
+    CKS(ws(B_HI0, (size_t)slot_h * B * 2, &hi[0]));
+    CKS(ws(B_HI1, (size_t)slot_h * B * 2, &hi[1]));
+    if (split) {
+      CKS(ws(B_LO0, (size_t)slot_h * B * 2, &lo[0]));
+      CKS(ws(B_LO1, (size_t)slot_h * B * 2, &lo[1]));
+    }
+    CKS(tmaps_for(hi[0], lo[0], N, B, ld_h, slot_h, m[0]));
+    CKS(tmaps_for(hi[1], lo[1], N, B, ld_h, slot_h, m[1]));
+    A.ld_h = ld_h;
+    A.slot_h = slot_h;
+  } else {
+    // FFMA path: Y ping-pongs between two workspace buffers so the last layer
+    // (which writes X_out) never reads its own output
+    CKS(ws(B_Y0, (size_t)slot * B * 4, &Y[0]));
+    CKS(ws(B_Y1, (size_t)slot * B * 4, &Y[1]));
+  }
+  // input layer X_0 (no control step)
+  CK(launch_input_layer((const float* const*)hs, (const int*)ns, N, (float*)Y[0], N, slot, (__half*)hi[0],
+                        (__half*)lo[0],
+                        ld_h, slot_h, N, (int)ld_h, A.lo_scale, (Ctl*)ctl, nullptr, (double2*)part, (unsigned*)tick,
+                        g.shift, 0, B, igrid, st));
+  if (ckpt)
+    CK(launch_materialize((float*)Y[0], N, slot, N, B, (const double*)alpha, ckpt_slot(0), N, slot, mgrid, st));
+  for (int n = 0; n < L; ++n) {
+    const int cur = n & 1;
+    float* Yc = (float*)Y[tc ? 0 : cur];
+    CK(launch_rownorm(Yc, N, slot, (const int*)ns, B, N, (double*)rn, N, nullptr, nullptr, nullptr, rgrid, st));
+    A.lp = (const LayerParams*)params + (size_t)n * B;
+    if (tc) {
+      A.Yin = X_out;
+      A.Yout = X_out;
+      A.hi_out = (__half*)hi[cur ^ 1];
+      A.lo_out = (__half*)lo[cur ^ 1];
+      CK(launch_syrk_tc(A, m[cur], split, std::min(ntiles, g.num_sms), st));
+    } else {
+      A.Yin = Yc;
+      A.Yout = (float*)Y[cur ^ 1];
+      CK(launch_syrk_simt(A, std::min(ntiles, 65535), st));
+    }
+    if (ckpt && (n + 1) % ckpt_every == 0) {
+      const int k = (n + 1) / ckpt_every;
+      if (n == L - 1) {
+        CK(cudaMemcpyAsync(ckpt_slot(k), X_out, (size_t)B * slot * 4, cudaMemcpyDeviceToDevice, st));
+      } else {
+        float* Yn = (float*)Y[tc ? 0 : (cur ^ 1)];
+        CK(launch_materialize(Yn, N, slot, N, B, (const double*)alpha + (size_t)(n + 1) * B, ckpt_slot(k), N, slot,
+                              mgrid, st));
+      }
+    }
+  }
+  return SP2_OK;
 }
 
 sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float* coef, int ckpt_every,
                                 const float* ckpt, const float* G_out, double* dcoef, float* G_in) {
-  (void)H; (void)B; (void)N; (void)L; (void)coef; (void)ckpt_every; (void)ckpt; (void)G_out; (void)dcoef; (void)G_in;
-  set_err("sp2_network_backward: not available in this build");
-  return SP2_ERR_UNSUPPORTED;
+  t_err.clear();
+  CKS(require_init());
+  if (!H || !ckpt || !G_out || !dcoef || !coef || B < 1 || B > 4096 || N < 1 || N > 8192 ||
+      (long long)B * N * N >= (1LL << 31) || L < 1 || L > 256 || ckpt_every < 1 || ckpt_every > L) {
+    set_err("sp2_network_backward: invalid argument");
+    return SP2_ERR_INVALID_ARG;
+  }
+  if (!tc_precision(g.precision)) {
+    set_err("sp2_network_backward: the adjoint runs on the tensor-core paths (split or fp16)");
+    return SP2_ERR_UNSUPPORTED;
+  }
+  const bool split = g.precision == SP2_PREC_SPLIT_FP16;
+  cudaStream_t st = g.stream;
+  const long long slot = (long long)N * N;
+  const int ce = ckpt_every;
+  void* G;
+  CKS(ws(B_G, (size_t)B * slot * 4, &G));
+  bool ok = false;
+  NetPlan plan;
+  void *ctl, *ns, *hs, *dptr;
+  CKS(network_prologue(H, B, N, L, coef, &ok, plan, &ctl, &ns, &hs, &dptr, (float*)G));
+
+  // backward coefficients: G_n = (2 a_n alpha_n + b_n) G + a_n (Y_n G + G Y_n)
+  std::vector<LayerParams> bp((size_t)L * B);
+  std::vector<double> nalpha(plan.alpha.size());
+  for (size_t i = 0; i < nalpha.size(); ++i) nalpha[i] = -plan.alpha[i];
+  for (int n = 0; n < L; ++n)
+    for (int b = 0; b < B; ++b) {
+      const double a = coef[3 * n], bb = coef[3 * n + 1], al = plan.alpha[(size_t)n * B + b];
+      LayerParams p;
+      memset(&p, 0, sizeof(p));
+      p.ca_d = 2.0 * a * al + bb;
+      p.cb_d = a;
+      p.cc_d = 0.0;
+      p.ca = (float)p.ca_d;
+      p.cb = (float)p.cb_d;
+      p.active = 1;
+      p.out_mode = OUT_Y;
+      bp[(size_t)n * B + b] = p;
+      // forward recomputation never reaches the last layer: keep OUT_Y there
+      plan.params[(size_t)n * B + b].out_mode = OUT_Y;
+      plan.params[(size_t)n * B + b].alpha_out = 0.0;
+    }
+  int ntiles = 0;
+  CKS(upload_tiles(N, B, true, &ntiles));
+  const long long ld_h = round_up(N, 64), slot_h = ld_h * N;
+  void *params, *params2, *nal, *rn, *err, *seg, *yh, *yl = nullptr, *gh[2], *gl[2] = {nullptr, nullptr}, *dots,
+       *tdots;
+  CKS(ws(B_PARAMS, plan.params.size() * sizeof(LayerParams), &params));
+  CKS(ws(B_PARAMS2, bp.size() * sizeof(LayerParams), &params2));
+  CKS(ws(B_NALPHA, nalpha.size() * sizeof(double), &nal));
+  CKS(ws(B_RN, (size_t)B * N * sizeof(double), &rn));
+  CKS(ws(B_ERR, sizeof(int), &err, true));
+  CKS(ws(B_SEG, (size_t)ce * B * slot * 4, &seg));
+  CKS(ws(B_HI0, (size_t)slot_h * B * 2, &yh));
+  CKS(ws(B_GH0, (size_t)slot_h * B * 2, &gh[0]));
+  CKS(ws(B_GH1, (size_t)slot_h * B * 2, &gh[1]));
+  if (split) {
+    CKS(ws(B_LO0, (size_t)slot_h * B * 2, &yl));
+    CKS(ws(B_GL0, (size_t)slot_h * B * 2, &gl[0]));
+    CKS(ws(B_GL1, (size_t)slot_h * B * 2, &gl[1]));
+  }
+  CKS(ws(B_DOTS, (size_t)L * B * 3 * sizeof(double), &dots, true));
+  CKS(ws(B_TDOTS, (size_t)ntiles * 3 * sizeof(double), &tdots));
+  void* h;
+  const size_t pb = plan.params.size() * sizeof(LayerParams), bb2 = bp.size() * sizeof(LayerParams),
+               ab = nalpha.size() * sizeof(double);
+  CKS(staging(pb + bb2 + ab, &h));
+  memcpy(h, plan.params.data(), pb);
+  memcpy((char*)h + pb, bp.data(), bb2);
+  memcpy((char*)h + pb + bb2, nalpha.data(), ab);
+  CK(cudaMemcpyAsync(params, h, pb, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(params2, (char*)h + pb, bb2, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(nal, (char*)h + pb + bb2, ab, cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(g.stage_done, st));
+
+  CUtensorMap mY[4], mG[2][4];
+  CKS(tmaps_for(yh, yl, N, B, ld_h, slot_h, mY));
+  CKS(tmaps_for(gh[0], gl[0], N, B, ld_h, slot_h, mG[0]));
+  CKS(tmaps_for(gh[1], gl[1], N, B, ld_h, slot_h, mG[1]));
+  const float ls = std::ldexp(1.0f, g.lo_scale_exp);
+  SqArgs A;
+  memset(&A, 0, sizeof(A));
+  A.Dptr = (float* const*)dptr;
+  A.Ns = (const int*)ns;
+  A.tiles = (const uint32_t*)g.buf[B_TILES].p;
+  A.ntiles = ntiles;
+  A.tile_off = (const int*)g.buf[B_TOFF].p;
+  A.tile_cnt = (const int*)g.buf[B_TCNT].p;
+  A.lp_per_instance = 1;
+  A.tile_part = (double2*)g.buf[B_TPART].p;
+  A.inst_done = (unsigned*)g.buf[B_IDONE].p;
+  A.lo_scale = ls;
+  A.lo_unscale = std::ldexp(1.0f, -g.lo_scale_exp);
+  A.err = (int*)err;
+  A.ld_y = N;
+  A.slot_y = slot;
+  A.ld_h = ld_h;
+  A.slot_h = slot_h;
+  const int sgrid = (int)std::min<long long>((long long)N * B, 8LL * g.num_sms);
+  const int mgrid = (int)std::min<long long>(N, std::max(1, 4 * g.num_sms / B + 1));
+  const int rgrid = (int)std::min<long long>((N + 7) / 8, std::max(1, 2 * g.num_sms / B + 1));
+  const int tgrid = std::min(ntiles, g.num_sms);
+  auto segY = [&](int i) { return (float*)seg + (size_t)i * B * slot; };
+
+  CK(cudaMemcpyAsync(G, G_out, (size_t)B * slot * 4, cudaMemcpyDeviceToDevice, st));
+  CK(launch_split_pad((float*)G, N, slot, N, B, ls, (__half*)gh[0], (__half*)gl[0], ld_h, slot_h, sgrid, st));
+  int cur = 0;
+  const int nseg_layers = (L + ce - 1) / ce;
+  for (int sgi = nseg_layers - 1; sgi >= 0; --sgi) {
+    const int n0 = sgi * ce, n1 = std::min(n0 + ce, L);
+    // Y_{n0} = X_{n0} - alpha_{n0} I from the checkpoint, then recompute to Y_{n1-1}
+    CK(launch_materialize(ckpt + (size_t)sgi * B * slot, N, slot, N, B, (const double*)nal + (size_t)n0 * B,
+                          segY(0), N, slot, mgrid, st));
+    for (int n = n0; n + 1 < n1; ++n) {
+      float* Yn = segY(n - n0);
+      CK(launch_rownorm(Yn, N, slot, (const int*)ns, B, N, (double*)rn, N, nullptr, nullptr, nullptr, rgrid, st));
+      CK(launch_split_pad(Yn, N, slot, N, B, ls, (__half*)yh, (__half*)yl, ld_h, slot_h, sgrid, st));
+      SqArgs F = A;
+      F.Yin = Yn;
+      F.Yout = segY(n + 1 - n0);
+      F.rn = (const double*)rn;
+      F.ld_rn = N;
+      F.lp = (const LayerParams*)params + (size_t)n * B;
+      F.nseg = 1;
+      CK(launch_syrk_tc(F, mY, split, tgrid, st));
+    }
+    for (int n = n1 - 1; n >= n0; --n) {
+      float* Yn = segY(n - n0);
+      CK(launch_split_pad(Yn, N, slot, N, B, ls, (__half*)yh, (__half*)yl, ld_h, slot_h, sgrid, st));
+      CUtensorMap m8[8] = {mY[0], mY[1], mG[cur][2], mG[cur][3], mG[cur][0], mG[cur][1], mY[2], mY[3]};
+      SqArgs Bk = A;
+      Bk.Yin = (float*)G;
+      Bk.Yout = (float*)G;
+      Bk.hi_out = (__half*)gh[cur ^ 1];
+      Bk.lo_out = (__half*)gl[cur ^ 1];
+      Bk.rn = nullptr;
+      Bk.lp = (const LayerParams*)params2 + (size_t)n * B;
+      Bk.nseg = 2;
+      Bk.aux = Yn;
+      Bk.tile_dots = (double*)tdots;
+      Bk.dots_out = (double*)dots + (size_t)n * B * 3;
+      CK(launch_syrk_tc(Bk, m8, split, tgrid, st));
+      cur ^= 1;
+    }
+  }
+  if (G_in) CK(cudaMemcpyAsync(G_in, G, (size_t)B * slot * 4, cudaMemcpyDeviceToDevice, st));
+  void* hd;
+  CKS(staging((size_t)L * B * 3 * sizeof(double) + 16, &hd));
+  CK(cudaMemcpyAsync(hd, dots, (size_t)L * B * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync((char*)hd + (size_t)L * B * 3 * sizeof(double), err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double* dd = (const double*)hd;
+  if (*(const int*)((char*)hd + (size_t)L * B * 3 * sizeof(double))) {
+    set_err("a bounded device wait timed out");
+    return SP2_ERR_DEVICE_TIMEOUT;
+  }
+  // dL/da_n = <G, X_n^2> = alpha^2 tr G + 2 alpha <G, Y_n> + <Y_n G + G Y_n, Y_n> / 2
+  // dL/db_n = <G, X_n>   = alpha tr G + <G, Y_n>;   dL/dc_n = tr G
+  for (int n = 0; n < L; ++n) {
+    double da = 0.0, db = 0.0, dc = 0.0;
+    for (int b = 0; b < B; ++b) {
+      const double al = plan.alpha[(size_t)n * B + b];
+      const double* v = dd + ((size_t)n * B + b) * 3;
+      da += al * al * v[0] + 2.0 * al * v[1] + 0.5 * v[2];
+      db += al * v[0] + v[1];
+      dc += v[0];
+    }
+    dcoef[3 * n] = da;
+    dcoef[3 * n + 1] = db;
+    dcoef[3 * n + 2] = dc;
+  }
+  return SP2_OK;
 }
 
 }  // extern "C"

@@ -40,6 +40,10 @@ struct SqArgs {
   double* traces_out;      // [batch][2] when ctl == nullptr, or nullptr
   const double* rn;        // [batch][ld_rn] FP64 row norms sum_k Y[r][k]^2 = (Y^2)_rr of the input
   long long ld_rn;
+  int nseg;                // 1: P = Y Y (one operand); 2: P = A B^T + B A^T (second map set)
+  const float* aux;        // adjoint mode: Y_n, same layout as Yin; dots <P, aux>, <Yin, aux>
+  double* tile_dots;       // [ntiles][3] per-tile (tr Yin, <Yin, aux>, <P, aux>) in adjoint mode
+  double* dots_out;        // [batch][3] per-instance sums of tile_dots
   float lo_scale;          // 2^s
   float lo_unscale;        // 2^-s
   int* err;                // device error word (SP2_ERR_DEVICE_TIMEOUT on a timed-out wait)
@@ -61,6 +65,8 @@ cudaError_t launch_split(const float* X, long long n, float lo_scale, __half* hi
                          cudaStream_t st);
 cudaError_t launch_split_pad(const float* X, long long ld_x, long long slot_x, int N, int B, float lo_scale,
                              __half* hi, __half* lo, long long ld_h, long long slot_h, int grid, cudaStream_t st);
+cudaError_t launch_materialize(const float* Y, long long ld_y, long long slot_y, int N, int B, const double* alpha,
+                               float* out, long long ld_o, long long slot_o, int grid_x, cudaStream_t st);
 cudaError_t launch_observable(const float* D, const float* A, long long n, double* block_out, int grid,
                               cudaStream_t st);
 
@@ -74,7 +80,8 @@ cudaError_t launch_rownorm(const float* Y, long long ld_y, long long slot_y, con
 cudaError_t launch_syrk_simt(const SqArgs& a, int grid, cudaStream_t st);
 
 // Tensor-core squaring.  tmaps: {hi(A box), lo(A box), hi(B box), lo(B box)}
-// over the current split buffers.  split = false: plain FP16 (hi only).
+// over the current split buffers, followed (nseg == 2) by the four maps of
+// the second K segment.  split = false: plain FP16 (hi only).
 cudaError_t launch_syrk_tc(const SqArgs& a, const CUtensorMap* tmaps, bool split, int grid, cudaStream_t st);
 size_t syrk_tc_smem_bytes(bool split);
 

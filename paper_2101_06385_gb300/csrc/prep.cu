@@ -378,6 +378,24 @@ __global__ void split_pad_kernel(const float* __restrict__ X, long long ld_x, lo
   }
 }
 
+// ---------------------------------------------------------------- materialise
+// out[b] = Y[b] + alpha[b] I (FP64 add on the diagonal, one rounding): the
+// full iterate X = alpha I + Y, e.g. for a network checkpoint.
+__global__ void materialize_kernel(const float* __restrict__ Y, long long ld_y, long long slot_y, int N,
+                                   const double* __restrict__ alpha, float* __restrict__ out, long long ld_o,
+                                   long long slot_o) {
+  const int b = blockIdx.y;
+  const double a = alpha[b];
+  for (int r = blockIdx.x; r < N; r += gridDim.x) {
+    const float* yr = Y + (long long)b * slot_y + (long long)r * ld_y;
+    float* orow = out + (long long)b * slot_o + (long long)r * ld_o;
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+      const float y = yr[c];
+      orow[c] = (r == c) ? (float)((double)y + a) : y;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- observable
 __global__ void __launch_bounds__(256) observable_kernel(const float* __restrict__ D, const float* __restrict__ A,
                                                          long long n, double* __restrict__ block_out) {
@@ -450,6 +468,13 @@ cudaError_t launch_split(const float* X, long long n, float lo_scale, __half* hi
 cudaError_t launch_split_pad(const float* X, long long ld_x, long long slot_x, int N, int B, float lo_scale,
                              __half* hi, __half* lo, long long ld_h, long long slot_h, int grid, cudaStream_t st) {
   split_pad_kernel<<<grid, 256, 0, st>>>(X, ld_x, slot_x, N, B, lo_scale, hi, lo, ld_h, slot_h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_materialize(const float* Y, long long ld_y, long long slot_y, int N, int B, const double* alpha,
+                               float* out, long long ld_o, long long slot_o, int grid_x, cudaStream_t st) {
+  dim3 grid(grid_x, B);
+  materialize_kernel<<<grid, 256, 0, st>>>(Y, ld_y, slot_y, N, alpha, out, ld_o, slot_o);
   return cudaGetLastError();
 }
 

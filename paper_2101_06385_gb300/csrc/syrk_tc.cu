@@ -174,6 +174,8 @@ template <bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)
     syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_hiA, const __grid_constant__ CUtensorMap tm_loA,
                    const __grid_constant__ CUtensorMap tm_hiB, const __grid_constant__ CUtensorMap tm_loB,
+                   const __grid_constant__ CUtensorMap tm_hiA2, const __grid_constant__ CUtensorMap tm_loA2,
+                   const __grid_constant__ CUtensorMap tm_hiB2, const __grid_constant__ CUtensorMap tm_loB2,
                    const SqArgs a) {
   constexpr int STAGES = SPLIT ? STAGES_SPLIT : STAGES_PLAIN;
   constexpr int STAGE_BYTES = SPLIT ? STAGE_SPLIT : STAGE_PLAIN;
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* drain = tmem_empty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   __shared__ int s_abort;
-  __shared__ double s_red[4][2];
+  __shared__ double s_red[4][5];
   __shared__ int s_got[4];
 
   const int warp = threadIdx.x >> 5;
@@ -232,22 +234,29 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int N = a.Ns[b];
         const int rowA = I * BN + h * BM, rowB = J * BN;
         const int nk = (N + BK - 1) / BK;
-        for (int kb = 0; kb < nk; ++kb) {
+        const int nseg = a.nseg > 1 ? 2 : 1;
+        for (int kb = 0; kb < nk * nseg; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
             ok = false;
             break;
           }
           uint8_t* st = smem + stage * STAGE_BYTES;
           mbar_expect_tx(&full[stage], STAGE_BYTES);
-          const int k0 = kb * BK;
+          // second K segment (two-operand product A B^T + B A^T): swap the maps
+          const bool seg2 = kb >= nk;
+          const int k0 = (seg2 ? kb - nk : kb) * BK;
+          const CUtensorMap* mhA = seg2 ? &tm_hiA2 : &tm_hiA;
+          const CUtensorMap* mlA = seg2 ? &tm_loA2 : &tm_loA;
+          const CUtensorMap* mhB = seg2 ? &tm_hiB2 : &tm_hiB;
+          const CUtensorMap* mlB = seg2 ? &tm_loB2 : &tm_loB;
           if (SPLIT) {
-            tma_load_3d(st, &tm_hiA, k0, rowA, b, &full[stage]);
-            tma_load_3d(st + A_BYTES, &tm_loA, k0, rowA, b, &full[stage]);
-            tma_load_3d(st + 2 * A_BYTES, &tm_hiB, k0, rowB, b, &full[stage]);
-            tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tm_loB, k0, rowB, b, &full[stage]);
+            tma_load_3d(st, mhA, k0, rowA, b, &full[stage]);
+            tma_load_3d(st + A_BYTES, mlA, k0, rowA, b, &full[stage]);
+            tma_load_3d(st + 2 * A_BYTES, mhB, k0, rowB, b, &full[stage]);
+            tma_load_3d(st + 2 * A_BYTES + B_BYTES, mlB, k0, rowB, b, &full[stage]);
           } else {
-            tma_load_3d(st, &tm_hiA, k0, rowA, b, &full[stage]);
-            tma_load_3d(st + A_BYTES, &tm_hiB, k0, rowB, b, &full[stage]);
+            tma_load_3d(st, mhA, k0, rowA, b, &full[stage]);
+            tma_load_3d(st + A_BYTES, mhB, k0, rowB, b, &full[stage]);
           }
           ++armed[stage];
           if (++stage == STAGES) {
@@ -287,7 +296,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         acc_phase ^= 1u;
         tc_fence_after();
-        for (int kb = 0; kb < nk; ++kb) {
+        const int nseg = a.nseg > 1 ? 2 : 1;
+        for (int kb = 0; kb < nk * nseg; ++kb) {
           if (!mbar_wait(&full[stage], phase, abort_flag)) {
             ok = false;
             break;
@@ -367,6 +377,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const long long ldh = a.ld_h;
       float* D = outD ? a.Dptr[b] : nullptr;
       double tr = 0.0, sq = 0.0;
+      double dtr = 0.0, dgy = 0.0, dpy = 0.0;  // adjoint-mode dot products
       const uint32_t lane_base = (uint32_t)(q * 32) << 16;
 
       for (int ch = 0; ch < BN / 32; ++ch) {
@@ -394,6 +405,23 @@ __global__ void __launch_bounds__(THREADS, 1)
           } else {
 #pragma unroll
             for (int j = 0; j < 32; ++j) y[j] = (c0 + j < N) ? Yold[(long long)r * ld + c0 + j] : 0.f;
+          }
+          if (a.aux) {
+            // adjoint mode: tr Yin, <Yin, aux>, <P, aux> on the old values
+            const float* ax = a.aux + (long long)b * a.slot_y + (long long)r * ld + c0;
+            float gy = 0.f, py = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (c0 + j < N) {
+                const float xv = ax[j];
+                const float P = SPLIT ? fmaf(v1[j], a.lo_unscale, v0[j]) : v0[j];
+                gy = fmaf(y[j], xv, gy);
+                py = fmaf(P, xv, py);
+                if (r == c0 + j) dtr += (double)y[j];
+              }
+            }
+            dgy += (double)gy;
+            dpy += (double)py;
           }
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
@@ -484,21 +512,43 @@ __global__ void __launch_bounds__(THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(tmem_empty);
 
-      if (mirror) sq *= 2.0;
+      if (mirror) {
+        sq *= 2.0;
+        dgy *= 2.0;
+        dpy *= 2.0;
+      }
       tr = warp_sum_d(tr);
       sq = warp_sum_d(sq);
+      if (a.aux) {
+        dtr = warp_sum_d(dtr);
+        dgy = warp_sum_d(dgy);
+        dpy = warp_sum_d(dpy);
+      }
       if (lane == 0) {
         s_red[q][0] = tr;
         s_red[q][1] = sq;
+        s_red[q][2] = dtr;
+        s_red[q][3] = dgy;
+        s_red[q][4] = dpy;
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (warp == 2) {
         double T = 0.0, Q = 0.0;
-        if (lane == 0)
+        if (lane == 0) {
+          double d0 = 0.0, d1 = 0.0, d2 = 0.0;
           for (int k = 0; k < 4; ++k) {
             T += s_red[k][0];
             Q += s_red[k][1];
+            d0 += s_red[k][2];
+            d1 += s_red[k][3];
+            d2 += s_red[k][4];
           }
+          if (a.aux) {
+            a.tile_dots[3 * (long long)t + 0] = d0;
+            a.tile_dots[3 * (long long)t + 1] = d1;
+            a.tile_dots[3 * (long long)t + 2] = d2;
+          }
+        }
         finish_tile_warp(a, t, b, T, Q, p.out_mode);
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -523,16 +573,20 @@ size_t syrk_tc_smem_bytes(bool split) {
 }
 
 cudaError_t launch_syrk_tc(const SqArgs& a, const CUtensorMap* tm, bool split, int grid, cudaStream_t st) {
+  // one K segment uses tm[0..3]; two segments also tm[4..7]
+  const CUtensorMap* t2 = (a.nseg == 2) ? tm + 4 : tm;
   const size_t smem = syrk_tc_smem_bytes(split);
   cudaError_t e;
   if (split) {
     e = cudaFuncSetAttribute(tc::syrk_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    tc::syrk_tc_kernel<true><<<grid, tc::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], a);
+    tc::syrk_tc_kernel<true><<<grid, tc::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], t2[0], t2[1], t2[2],
+                                                              t2[3], a);
   } else {
     e = cudaFuncSetAttribute(tc::syrk_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    tc::syrk_tc_kernel<false><<<grid, tc::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], a);
+    tc::syrk_tc_kernel<false><<<grid, tc::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], t2[0], t2[1], t2[2],
+                                                               t2[3], a);
   }
   return cudaGetLastError();
 }

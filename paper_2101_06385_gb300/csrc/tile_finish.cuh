@@ -35,7 +35,24 @@ __device__ inline void finish_tile_warp(const SqArgs& a, int t, int b, double tr
   }
   T = warp_sum_d(T);
   Q = warp_sum_d(Q);
+  double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+  if (a.dots_out) {
+    for (int k = lane; k < cnt; k += 32) {
+      const double* td = a.tile_dots + 3 * (long long)(off + k);
+      d0 += __ldcg(td);
+      d1 += __ldcg(td + 1);
+      d2 += __ldcg(td + 2);
+    }
+    d0 = warp_sum_d(d0);
+    d1 = warp_sum_d(d1);
+    d2 = warp_sum_d(d2);
+  }
   if (lane == 0) {
+    if (a.dots_out) {
+      a.dots_out[3 * b + 0] = d0;
+      a.dots_out[3 * b + 1] = d1;
+      a.dots_out[3 * b + 2] = d2;
+    }
     a.inst_done[b] = 0u;
     if (a.ctl) {
       if (out_mode == OUT_D)

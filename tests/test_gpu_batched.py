@@ -1,0 +1,79 @@
+"""Batched SP2 (many Hamiltonians of uneven size in grouped launches) against
+the FP64 closed form, instance by instance."""
+import numpy as np
+import pytest
+
+import oracle as o
+import sp2_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sp2():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2101_06385_gb300 as m
+
+    m.init(0)
+    return m
+
+
+def _check(hs, Ds, stats, tol=5e-5):
+    for h, D, st in zip(hs, Ds, stats):
+        m = o.error_metrics(D.cpu().numpy().astype(np.float64), o.density_matrix_closed_form(h.Q, h.n_occ),
+                            h.n_occ)
+        assert st.status == 0, st
+        assert m["max_abs"] <= tol and m["trace_err"] <= 1e-4, (h.N, m, st.iterations)
+
+
+@pytest.mark.parametrize("prec", ["split", "fp32"])
+def test_batched_uneven_sizes(sp2, prec):
+    sizes = [64, 96, 1000, 130, 257, 512, 33, 700, 1, 2, 384, 1024]
+    hs = []
+    for i, N in enumerate(sizes):
+        n_occ = max(0, min(N, N // 2 + (i % 3) - 1))
+        gap = 0.05 + 0.02 * i
+        hs.append(si.gapped_hamiltonian(N, n_occ, (-1.0, -gap / 2), (gap / 2, 1.0), seed=100 + i))
+    Hs = [torch.from_numpy(h.h32()).cuda() for h in hs]
+    sp2.set_precision(prec)
+    Ds, stats = sp2.density_matrix_batched(Hs, [h.n_occ for h in hs])
+    sp2.set_precision("split")
+    _check(hs, Ds, stats)
+    # each instance follows its own branch sequence: same as solving it alone
+    for h, H, st in zip(hs[:4], Hs[:4], stats[:4]):
+        _, s1 = sp2.density_matrix(H, h.n_occ, precision=prec)
+        k = min(len(s1.sigmas), len(st.sigmas)) - 4
+        assert s1.sigmas[:k] == st.sigmas[:k]
+
+
+def test_batched_config_sample(sp2):
+    """The 512-instance workload (N in {64..1024} step 32, gaps in [0.05, 0.3]),
+    checked on a sample of instances."""
+    cfg = si.batched_config()
+    rng = np.random.default_rng(5)
+    pick = set(rng.choice(len(cfg), 12, replace=False).tolist())
+    Hs, keep = [], {}
+    for i, (N, n_occ, gap, seed) in enumerate(cfg):
+        if i in pick:
+            h = si.batched_instance(N, n_occ, gap, seed)
+            keep[i] = h
+            Hs.append(torch.from_numpy(h.h32()).cuda())
+        else:
+            # unsampled instances: same construction, cheaper eigenvectors are not needed
+            h = si.batched_instance(N, n_occ, gap, seed)
+            Hs.append(torch.from_numpy(h.h32()).cuda())
+    Ds, stats = sp2.density_matrix_batched(Hs, [c[1] for c in cfg])
+    iters = [s.iterations for s in stats]
+    print(f"batched 512: layers min {min(iters)} max {max(iters)} mean {np.mean(iters):.1f}, time {stats[0].time_ms:.1f} ms")
+    assert all(s.status == 0 for s in stats)
+    _check([keep[i] for i in sorted(keep)], [Ds[i] for i in sorted(keep)], [stats[i] for i in sorted(keep)])
+
+
+def test_batched_reports_a_bad_instance(sp2):
+    good = si.gapped_hamiltonian(100, 50, seed=1)
+    Hs = [torch.from_numpy(good.h32()).cuda(), torch.eye(64, device="cuda") * 0.3]
+    with pytest.raises(sp2.SP2Error) as e:
+        sp2.density_matrix_batched(Hs, [50, 10])
+    assert e.value.status == -3

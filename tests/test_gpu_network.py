@@ -1,0 +1,97 @@
+"""Differentiable SP2 network (Eq. 16 in matrix form) on the GPU against the
+FP64 oracle: forward layers and checkpoints, and the hand-written adjoint
+(coefficient gradients and dL/dX_0)."""
+import numpy as np
+import pytest
+
+import oracle as o
+import sp2_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sp2():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2101_06385_gb300 as m
+
+    m.init(0)
+    m.set_precision("split")
+    return m
+
+
+def _instances(B, N, seed0):
+    return [si.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), seed=seed0 + i) for i in range(B)]
+
+
+def _oracle_x0(hs):
+    X0 = []
+    for h in hs:
+        H64 = h.h32().astype(np.float64)
+        lo, hi = o.gershgorin_bounds(H64)
+        X0.append(o.input_layer(H64, lo, hi))
+    return np.stack(X0)
+
+
+def _coef(hs, L, rng, jitter):
+    r = o.sp2(hs[0].h32().astype(np.float64), hs[0].n_occ, max_iter=L, refine=False)
+    coef = o.sp2_branch_coefficients(r.sigmas, L)
+    return coef + rng.uniform(-jitter, jitter, coef.shape)
+
+
+@pytest.mark.parametrize("B,N,L,ce", [(3, 300, 6, 2), (2, 512, 9, 4)])
+def test_forward_matches_oracle(sp2, B, N, L, ce):
+    rng = np.random.default_rng(N)
+    hs = _instances(B, N, 3000)
+    coef = _coef(hs, L, rng, 0.02).astype(np.float32)
+    H = torch.from_numpy(np.stack([h.h32() for h in hs])).cuda()
+    X, ck, bounds = sp2.network_forward(H, coef, ckpt_every=ce)
+    X0 = _oracle_x0(hs)
+    XL, xs = o.network_forward(X0, coef.astype(np.float64), keep=True)
+    err = np.max(np.abs(X.cpu().numpy() - XL))
+    print(f"forward B={B} N={N} L={L}: max-abs {err:.2e}")
+    assert err <= 1e-4
+    for k in range(L // ce + 1):
+        assert np.max(np.abs(ck[k].cpu().numpy() - xs[k * ce])) <= 1e-4
+    for b, h in enumerate(hs):
+        lo, hi = o.gershgorin_bounds(h.h32().astype(np.float64))
+        assert abs(bounds[b, 0].item() - lo) <= 1e-6 * abs(lo) and abs(bounds[b, 1].item() - hi) <= 1e-6 * abs(hi)
+
+
+@pytest.mark.parametrize("B,N,L,ce", [(2, 300, 6, 2), (2, 640, 8, 3)])
+def test_adjoint_matches_oracle(sp2, B, N, L, ce):
+    rng = np.random.default_rng(7 + N)
+    hs = _instances(B, N, 4000)
+    coef = _coef(hs, L, rng, 0.05).astype(np.float32)
+    H = torch.from_numpy(np.stack([h.h32() for h in hs])).cuda()
+    X, ck, _ = sp2.network_forward(H, coef, ckpt_every=ce)
+    target = np.stack([o.fermi_dirac_closed_form(h.Q, h.eps, 0.0, 0.05) for h in hs])
+    # loss = (1/B) sum_b ||X_L - D_FD||_F^2  ->  G_L = 2 (X_L - D_FD) / B
+    G_L = (2.0 * (X.cpu().numpy().astype(np.float64) - target) / B).astype(np.float32)
+    dcoef, G0 = sp2.network_backward(H, coef, ce, ck, torch.from_numpy(G_L).cuda())
+    X0 = _oracle_x0(hs)
+    want_d, want_G0 = o.network_adjoint(X0, coef.astype(np.float64), G_L.astype(np.float64))
+    d = dcoef.numpy()
+    rel = np.max(np.abs(d - want_d)) / np.max(np.abs(want_d))
+    g0 = np.max(np.abs(G0.cpu().numpy() - want_G0)) / np.max(np.abs(want_G0))
+    print(f"adjoint B={B} N={N} L={L}: dcoef rel {rel:.2e}, G0 rel {g0:.2e}")
+    assert rel <= 1e-3
+    assert g0 <= 1e-3
+
+
+def test_autograd_function(sp2):
+    rng = np.random.default_rng(1)
+    hs = _instances(2, 256, 5000)
+    L = 5
+    coef = torch.tensor(_coef(hs, L, rng, 0.02), dtype=torch.float32, requires_grad=True)
+    H = torch.from_numpy(np.stack([h.h32() for h in hs])).cuda()
+    X = sp2.SP2Network.apply(H, coef, 1)
+    target = torch.from_numpy(np.stack([o.fermi_dirac_closed_form(h.Q, h.eps, 0.0, 0.05) for h in hs])).float().cuda()
+    loss = ((X - target) ** 2).sum() / 2
+    loss.backward()
+    X0 = _oracle_x0(hs)
+    XL = o.network_forward(X0, coef.detach().numpy().astype(np.float64))
+    want, _ = o.network_adjoint(X0, coef.detach().numpy().astype(np.float64), 2.0 * (XL - target.cpu().numpy()) / 2)
+    assert np.max(np.abs(coef.grad.numpy() - want)) <= 1e-3 * np.max(np.abs(want))
