@@ -58,7 +58,7 @@ void set_err(const char* fmt, ...) {
 enum BufId {
   B_HI0, B_LO0, B_HI1, B_LO1, B_Y0, B_Y1, B_CTL, B_TILES, B_TOFF, B_TCNT, B_TPART, B_IDONE,
   B_PART, B_TICKET, B_ERR, B_DPTR, B_NS, B_HS, B_TRACES, B_PARAMS, B_BOUNDS, B_RN, B_PART2,
-  B_G, B_SEG, B_GH0, B_GL0, B_GH1, B_GL1, B_DOTS, B_TDOTS, B_PARAMS2, B_NALPHA, B_COUNT
+  B_G, B_SEG, B_GH0, B_GL0, B_GH1, B_GL1, B_DOTS, B_TDOTS, B_PARAMS2, B_NALPHA, B_HP0, B_HP1, B_COUNT
 };
 
 struct Buf {
@@ -225,6 +225,24 @@ sp2_status tmaps_for(const void* hi, const void* lo, int N, int B, long long ld_
             make_tmap_f16(&m[1], lo_, N, N, B, ld_h, slot_h, 32, kTcBM) &&
             make_tmap_f16(&m[2], hi, N, N, B, ld_h, slot_h, 32, kTcBN) &&
             make_tmap_f16(&m[3], lo_, N, N, B, ld_h, slot_h, 32, kTcBN);
+  if (!ok) {
+    set_err("cuTensorMapEncodeTiled failed (N=%d, ld=%lld)", N, ld_h);
+    return SP2_ERR_CUDA;
+  }
+  return SP2_OK;
+}
+
+// Tensor maps {hp(A box), lo(A box), hi(A box), hi(B box), lo(B box)} for the
+// single-accumulator squaring kernel (hp, lo may be null for plain FP16).
+sp2_status tmaps5_for(const void* hp, const void* lo, const void* hi, int N, int B, long long ld_h, long long slot_h,
+                      CUtensorMap* m) {
+  const void* hp_ = hp ? hp : hi;
+  const void* lo_ = lo ? lo : hi;
+  bool ok = make_tmap_f16(&m[0], hp_, N, N, B, ld_h, slot_h, 32, kTcBM) &&
+            make_tmap_f16(&m[1], lo_, N, N, B, ld_h, slot_h, 32, kTcBM) &&
+            make_tmap_f16(&m[2], hi, N, N, B, ld_h, slot_h, 32, kTcBM) &&
+            make_tmap_f16(&m[3], hi, N, N, B, ld_h, slot_h, 32, kTcBN) &&
+            make_tmap_f16(&m[4], lo_, N, N, B, ld_h, slot_h, 32, kTcBN);
   if (!ok) {
     set_err("cuTensorMapEncodeTiled failed (N=%d, ld=%lld)", N, ld_h);
     return SP2_ERR_CUDA;
@@ -507,19 +525,23 @@ sp2_status sp2_layer(const float* X, int B, int N, float a, float b, float c, fl
   A.ld_rn = N;
   if (tc) {
     const long long ld_h = round_up(N, 64), slot_h = ld_h * N;
-    void *hi, *lo = nullptr;
+    void *hi, *lo = nullptr, *hp = nullptr;
     CKS(ws(B_HI0, (size_t)slot_h * B * 2, &hi));
-    if (split) CKS(ws(B_LO0, (size_t)slot_h * B * 2, &lo));
+    if (split) {
+      CKS(ws(B_LO0, (size_t)slot_h * B * 2, &lo));
+      CKS(ws(B_HP0, (size_t)slot_h * B * 2, &hp));
+    }
     const int grid = (int)std::min<long long>((long long)N * B, 8LL * g.num_sms);
-    CK(launch_split_pad(X, N, (long long)N * N, N, B, A.lo_scale, (__half*)hi, (__half*)lo, ld_h, slot_h, grid,
+    CK(launch_split_pad(X, N, (long long)N * N, N, B, A.lo_scale, (__half*)hi, (__half*)lo, (__half*)hp, ld_h, slot_h, grid,
                         g.stream));
-    CUtensorMap m[4];
-    CKS(tmaps_for(hi, lo, N, B, ld_h, slot_h, m));
+    CUtensorMap m[5];
+    CKS(tmaps5_for(hp, lo, hi, N, B, ld_h, slot_h, m));
     A.hi_out = nullptr;
     A.lo_out = nullptr;
+    A.hp_out = nullptr;
     A.ld_h = ld_h;
     A.slot_h = slot_h;
-    CK(launch_syrk_tc(A, m, split, std::min(ntiles, g.num_sms), g.stream));
+    CK(launch_syrk_tc1(A, m, split, std::min(ntiles, g.num_sms), g.stream));
   } else {
     CK(launch_syrk_simt(A, ntiles, g.stream));
   }
@@ -610,25 +632,27 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
 
   if (tc) {
     const long long ld_h = round_up(N, 64), slot_h = ld_h * N;
-    void *hi[2], *lo[2] = {nullptr, nullptr};
+    void *hi[2], *lo[2] = {nullptr, nullptr}, *hp[2] = {nullptr, nullptr};
     CKS(ws(B_HI0, (size_t)slot_h * 2, &hi[0]));
     CKS(ws(B_HI1, (size_t)slot_h * 2, &hi[1]));
     if (split) {
       CKS(ws(B_LO0, (size_t)slot_h * 2, &lo[0]));
       CKS(ws(B_LO1, (size_t)slot_h * 2, &lo[1]));
+      CKS(ws(B_HP0, (size_t)slot_h * 2, &hp[0]));
+      CKS(ws(B_HP1, (size_t)slot_h * 2, &hp[1]));
     }
     // K2: Y_0 into D_out, split into buffer 0
     // Buffers hold N rows of ld_h columns; the tensor maps declare N x N, so
     // TMA zero-fills every element outside the matrix.
     CK(launch_input_layer((const float* const*)hs, (const int*)ns, N, D_out, N, (long long)N * N, (__half*)hi[0],
-                          (__half*)lo[0], ld_h, slot_h, N, (int)ld_h, A.lo_scale, (Ctl*)ctl, nullptr, (double2*)part,
-                          (unsigned*)tick, g.shift, 1, 1, igrid, st));
+                          (__half*)lo[0], (__half*)hp[0], ld_h, slot_h, N, (int)ld_h, A.lo_scale, (Ctl*)ctl, nullptr,
+                          (double2*)part, (unsigned*)tick, g.shift, 1, 1, igrid, st));
     // FP64 row norms of Y_0 and the first control step (sigma_1, IdErr_1)
     CK(launch_rownorm(D_out, N, (long long)N * N, (const int*)ns, 1, N, (double*)rn, N, (Ctl*)ctl, (double2*)part,
                       (unsigned*)tick, rgrid, st));
-    CUtensorMap m[2][4];
-    CKS(tmaps_for(hi[0], lo[0], N, 1, ld_h, slot_h, m[0]));
-    CKS(tmaps_for(hi[1], lo[1], N, 1, ld_h, slot_h, m[1]));
+    CUtensorMap m[2][5];
+    CKS(tmaps5_for(hp[0], lo[0], hi[0], N, 1, ld_h, slot_h, m[0]));
+    CKS(tmaps5_for(hp[1], lo[1], hi[1], N, 1, ld_h, slot_h, m[1]));
     A.Yin = D_out;
     A.Yout = D_out;
     A.ld_y = N;
@@ -641,7 +665,8 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
       const int cur = k & 1;
       A.hi_out = (__half*)hi[cur ^ 1];
       A.lo_out = (__half*)lo[cur ^ 1];
-      CK(launch_syrk_tc(A, m[cur], split, grid, st));
+      A.hp_out = (__half*)hp[cur ^ 1];
+      CK(launch_syrk_tc1(A, m[cur], split, grid, st));
       CK(launch_rownorm(D_out, N, (long long)N * N, (const int*)ns, 1, N, (double*)rn, N, (Ctl*)ctl, (double2*)part,
                         (unsigned*)tick, rgrid, st));
       CK(cudaEventRecord(g.lev[k + 1], st));
@@ -651,7 +676,7 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
     void* Y[2];
     CKS(ws(B_Y0, (size_t)slot_y * 4, &Y[0]));
     CKS(ws(B_Y1, (size_t)slot_y * 4, &Y[1]));
-    CK(launch_input_layer((const float* const*)hs, (const int*)ns, N, (float*)Y[0], ld_y, slot_y, nullptr, nullptr, 0,
+    CK(launch_input_layer((const float* const*)hs, (const int*)ns, N, (float*)Y[0], ld_y, slot_y, nullptr, nullptr, nullptr, 0,
                           0, N, N, A.lo_scale, (Ctl*)ctl, nullptr, (double2*)part, (unsigned*)tick, g.shift, 1, 1, igrid,
                           st));
     CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, 1, N, (double*)rn, N, (Ctl*)ctl, (double2*)part,
@@ -809,27 +834,32 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   CKS(ws(B_Y0, (size_t)slot_y * B * 4, &Y[0]));
   if (tc) {
     const long long ld_h = round_up(Nmax, 64), slot_h = ld_h * Nmax;
-    void *hi[2], *lo[2] = {nullptr, nullptr};
+    void *hi[2], *lo[2] = {nullptr, nullptr}, *hp[2] = {nullptr, nullptr};
     CKS(ws(B_HI0, (size_t)slot_h * B * 2, &hi[0]));
     CKS(ws(B_HI1, (size_t)slot_h * B * 2, &hi[1]));
     if (split) {
       CKS(ws(B_LO0, (size_t)slot_h * B * 2, &lo[0]));
       CKS(ws(B_LO1, (size_t)slot_h * B * 2, &lo[1]));
+      CKS(ws(B_HP0, (size_t)slot_h * B * 2, &hp[0]));
+      CKS(ws(B_HP1, (size_t)slot_h * B * 2, &hp[1]));
     }
     // Slots are Nmax x Nmax in the tensor maps: everything outside instance b's
     // N_b x N_b block must read as zero.  The input layer zero-fills buffer 0's
     // slot; the epilogues never write outside N_b x N_b (row tails up to the
     // 32-column chunk are written as zeros), so buffer 1 is cleared here.
     CK(cudaMemsetAsync(hi[1], 0, (size_t)slot_h * B * 2, st));
-    if (split) CK(cudaMemsetAsync(lo[1], 0, (size_t)slot_h * B * 2, st));
+    if (split) {
+      CK(cudaMemsetAsync(lo[1], 0, (size_t)slot_h * B * 2, st));
+      CK(cudaMemsetAsync(hp[1], 0, (size_t)slot_h * B * 2, st));
+    }
     CK(launch_input_layer((const float* const*)hs, (const int*)ns, 0, (float*)Y[0], ld_y, slot_y, (__half*)hi[0],
-                          (__half*)lo[0], ld_h, slot_h, Nmax, (int)ld_h, A.lo_scale, (Ctl*)ctl, nullptr,
+                          (__half*)lo[0], (__half*)hp[0], ld_h, slot_h, Nmax, (int)ld_h, A.lo_scale, (Ctl*)ctl, nullptr,
                           (double2*)part, (unsigned*)tick, g.shift, 1, B, igrid, st));
     CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
                       (double2*)part, (unsigned*)tick, rgrid, st));
-    CUtensorMap m[2][4];
-    CKS(tmaps_for(hi[0], lo[0], Nmax, B, ld_h, slot_h, m[0]));
-    CKS(tmaps_for(hi[1], lo[1], Nmax, B, ld_h, slot_h, m[1]));
+    CUtensorMap m[2][5];
+    CKS(tmaps5_for(hp[0], lo[0], hi[0], Nmax, B, ld_h, slot_h, m[0]));
+    CKS(tmaps5_for(hp[1], lo[1], hi[1], Nmax, B, ld_h, slot_h, m[1]));
     A.Yin = (float*)Y[0];
     A.Yout = (float*)Y[0];
     A.ld_y = ld_y;
@@ -842,14 +872,15 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
       const int cur = k & 1;
       A.hi_out = (__half*)hi[cur ^ 1];
       A.lo_out = (__half*)lo[cur ^ 1];
-      CK(launch_syrk_tc(A, m[cur], split, grid, st));
+      A.hp_out = (__half*)hp[cur ^ 1];
+      CK(launch_syrk_tc1(A, m[cur], split, grid, st));
       CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
                         (double2*)part, (unsigned*)tick, rgrid, st));
       CK(cudaEventRecord(g.lev[k + 1], st));
     }
   } else {
     CKS(ws(B_Y1, (size_t)slot_y * B * 4, &Y[1]));
-    CK(launch_input_layer((const float* const*)hs, (const int*)ns, 0, (float*)Y[0], ld_y, slot_y, nullptr, nullptr, 0,
+    CK(launch_input_layer((const float* const*)hs, (const int*)ns, 0, (float*)Y[0], ld_y, slot_y, nullptr, nullptr, nullptr, 0,
                           0, Nmax, Nmax, A.lo_scale, (Ctl*)ctl, nullptr, (double2*)part, (unsigned*)tick, g.shift, 1,
                           B, igrid, st));
     CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
@@ -1042,9 +1073,9 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
   auto ckpt_slot = [&](int k) { return ckpt + (size_t)k * B * slot; };
 
   void* Y[2] = {X_out, nullptr};
-  void *hi[2] = {nullptr, nullptr}, *lo[2] = {nullptr, nullptr};
+  void *hi[2] = {nullptr, nullptr}, *lo[2] = {nullptr, nullptr}, *hp[2] = {nullptr, nullptr};
   long long ld_h = 0, slot_h = 0;
-  CUtensorMap m[2][4];
+  CUtensorMap m[2][5];
   if (tc) {
     ld_h = round_up(N, 64);
     slot_h = ld_h * N;
@@ -1053,9 +1084,11 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
     if (split) {
       CKS(ws(B_LO0, (size_t)slot_h * B * 2, &lo[0]));
       CKS(ws(B_LO1, (size_t)slot_h * B * 2, &lo[1]));
+      CKS(ws(B_HP0, (size_t)slot_h * B * 2, &hp[0]));
+      CKS(ws(B_HP1, (size_t)slot_h * B * 2, &hp[1]));
     }
-    CKS(tmaps_for(hi[0], lo[0], N, B, ld_h, slot_h, m[0]));
-    CKS(tmaps_for(hi[1], lo[1], N, B, ld_h, slot_h, m[1]));
+    CKS(tmaps5_for(hp[0], lo[0], hi[0], N, B, ld_h, slot_h, m[0]));
+    CKS(tmaps5_for(hp[1], lo[1], hi[1], N, B, ld_h, slot_h, m[1]));
     A.ld_h = ld_h;
     A.slot_h = slot_h;
   } else {
@@ -1066,7 +1099,7 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
   }
   // input layer X_0 (no control step)
   CK(launch_input_layer((const float* const*)hs, (const int*)ns, N, (float*)Y[0], N, slot, (__half*)hi[0],
-                        (__half*)lo[0],
+                        (__half*)lo[0], (__half*)hp[0],
                         ld_h, slot_h, N, (int)ld_h, A.lo_scale, (Ctl*)ctl, nullptr, (double2*)part, (unsigned*)tick,
                         g.shift, 0, B, igrid, st));
   if (ckpt)
@@ -1081,7 +1114,8 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
       A.Yout = X_out;
       A.hi_out = (__half*)hi[cur ^ 1];
       A.lo_out = (__half*)lo[cur ^ 1];
-      CK(launch_syrk_tc(A, m[cur], split, std::min(ntiles, g.num_sms), st));
+      A.hp_out = (__half*)hp[cur ^ 1];
+      CK(launch_syrk_tc1(A, m[cur], split, std::min(ntiles, g.num_sms), st));
     } else {
       A.Yin = Yc;
       A.Yout = (float*)Y[cur ^ 1];
@@ -1157,7 +1191,9 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
   CKS(ws(B_RN, (size_t)B * N * sizeof(double), &rn));
   CKS(ws(B_ERR, sizeof(int), &err, true));
   CKS(ws(B_SEG, (size_t)ce * B * slot * 4, &seg));
+  void* yhp = nullptr;
   CKS(ws(B_HI0, (size_t)slot_h * B * 2, &yh));
+  if (split) CKS(ws(B_HP0, (size_t)slot_h * B * 2, &yhp));
   CKS(ws(B_GH0, (size_t)slot_h * B * 2, &gh[0]));
   CKS(ws(B_GH1, (size_t)slot_h * B * 2, &gh[1]));
   if (split) {
@@ -1179,8 +1215,9 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
   CK(cudaMemcpyAsync(nal, (char*)h + pb + bb2, ab, cudaMemcpyHostToDevice, st));
   CK(cudaEventRecord(g.stage_done, st));
 
-  CUtensorMap mY[4], mG[2][4];
+  CUtensorMap mY[4], mY5[5], mG[2][4];
   CKS(tmaps_for(yh, yl, N, B, ld_h, slot_h, mY));
+  CKS(tmaps5_for(yhp, yl, yh, N, B, ld_h, slot_h, mY5));
   CKS(tmaps_for(gh[0], gl[0], N, B, ld_h, slot_h, mG[0]));
   CKS(tmaps_for(gh[1], gl[1], N, B, ld_h, slot_h, mG[1]));
   const float ls = std::ldexp(1.0f, g.lo_scale_exp);
@@ -1209,7 +1246,7 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
   auto segY = [&](int i) { return (float*)seg + (size_t)i * B * slot; };
 
   CK(cudaMemcpyAsync(G, G_out, (size_t)B * slot * 4, cudaMemcpyDeviceToDevice, st));
-  CK(launch_split_pad((float*)G, N, slot, N, B, ls, (__half*)gh[0], (__half*)gl[0], ld_h, slot_h, sgrid, st));
+  CK(launch_split_pad((float*)G, N, slot, N, B, ls, (__half*)gh[0], (__half*)gl[0], nullptr, ld_h, slot_h, sgrid, st));
   int cur = 0;
   const int nseg_layers = (L + ce - 1) / ce;
   for (int sgi = nseg_layers - 1; sgi >= 0; --sgi) {
@@ -1220,7 +1257,7 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
     for (int n = n0; n + 1 < n1; ++n) {
       float* Yn = segY(n - n0);
       CK(launch_rownorm(Yn, N, slot, (const int*)ns, B, N, (double*)rn, N, nullptr, nullptr, nullptr, rgrid, st));
-      CK(launch_split_pad(Yn, N, slot, N, B, ls, (__half*)yh, (__half*)yl, ld_h, slot_h, sgrid, st));
+      CK(launch_split_pad(Yn, N, slot, N, B, ls, (__half*)yh, (__half*)yl, (__half*)yhp, ld_h, slot_h, sgrid, st));
       SqArgs F = A;
       F.Yin = Yn;
       F.Yout = segY(n + 1 - n0);
@@ -1228,11 +1265,11 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
       F.ld_rn = N;
       F.lp = (const LayerParams*)params + (size_t)n * B;
       F.nseg = 1;
-      CK(launch_syrk_tc(F, mY, split, tgrid, st));
+      CK(launch_syrk_tc1(F, mY5, split, tgrid, st));
     }
     for (int n = n1 - 1; n >= n0; --n) {
       float* Yn = segY(n - n0);
-      CK(launch_split_pad(Yn, N, slot, N, B, ls, (__half*)yh, (__half*)yl, ld_h, slot_h, sgrid, st));
+      CK(launch_split_pad(Yn, N, slot, N, B, ls, (__half*)yh, (__half*)yl, nullptr, ld_h, slot_h, sgrid, st));
       CUtensorMap m8[8] = {mY[0], mY[1], mG[cur][2], mG[cur][3], mG[cur][0], mG[cur][1], mY[2], mY[3]};
       SqArgs Bk = A;
       Bk.Yin = (float*)G;

@@ -25,6 +25,7 @@ struct SqArgs {
   long long ld_y, slot_y;
   __half* hi_out;          // split of the updated iterate (nullptr: not written)
   __half* lo_out;
+  __half* hp_out;          // 2^s * hi of the updated iterate (single-accumulator kernel), or nullptr
   long long ld_h, slot_h;
   float* const* Dptr;      // [batch] device array of output pointers (OUT_D)
   const int* Ns;           // [batch]
@@ -58,13 +59,14 @@ cudaError_t launch_gershgorin(const float* H, int N, long long ld, long long slo
                               unsigned* ticket, Ctl* ctl, double* bounds_out, int grid, cudaStream_t st);
 cudaError_t launch_gershgorin_batched(const float* const* Hs, const int* Ns, Ctl* ctl, int batch, cudaStream_t st);
 cudaError_t launch_input_layer(const float* const* Hs, const int* Ns, long long ld_in, float* Y, long long ld_y,
-                               long long slot_y, __half* hi, __half* lo, long long ld_h, long long slot_h, int rows_pad,
-                               int cols_pad, float lo_scale, Ctl* ctl, const double* bounds, double2* partials, unsigned* tickets,
+                               long long slot_y, __half* hi, __half* lo, __half* hp, long long ld_h, long long slot_h,
+                               int rows_pad, int cols_pad, float lo_scale, Ctl* ctl, const double* bounds, double2* partials, unsigned* tickets,
                                int shift, int ctl_step, int batch, int grid_x, cudaStream_t st);
 cudaError_t launch_split(const float* X, long long n, float lo_scale, __half* hi, __half* lo, int grid,
                          cudaStream_t st);
 cudaError_t launch_split_pad(const float* X, long long ld_x, long long slot_x, int N, int B, float lo_scale,
-                             __half* hi, __half* lo, long long ld_h, long long slot_h, int grid, cudaStream_t st);
+                             __half* hi, __half* lo, __half* hp, long long ld_h, long long slot_h, int grid,
+                             cudaStream_t st);
 cudaError_t launch_materialize(const float* Y, long long ld_y, long long slot_y, int N, int B, const double* alpha,
                                float* out, long long ld_o, long long slot_o, int grid_x, cudaStream_t st);
 cudaError_t launch_observable(const float* D, const float* A, long long n, double* block_out, int grid,
@@ -76,6 +78,13 @@ cudaError_t launch_observable(const float* D, const float* A, long long n, doubl
 cudaError_t launch_rownorm(const float* Y, long long ld_y, long long slot_y, const int* Ns, int batch, int max_rows,
                            double* rn, long long ld_rn, Ctl* ctl, double2* partials, unsigned* tickets, int grid_x,
                            cudaStream_t st);
+
+// Single-accumulator split squaring (tcgen05, double-buffered TMEM): the
+// three products 2^s hi hi + lo' hi + hi lo' go into one FP32 accumulator,
+// with hp = 2^s hi a third FP16 operand.  tmaps: {hp(A), lo(A), hi(A),
+// hi(B), lo(B)}; split = false: plain FP16, tmaps[2] = hi(A), tmaps[3] = hi(B).
+cudaError_t launch_syrk_tc1(const SqArgs& a, const CUtensorMap* tmaps, bool split, int grid, cudaStream_t st);
+size_t syrk_tc1_smem_bytes(bool split);
 
 cudaError_t launch_syrk_simt(const SqArgs& a, int grid, cudaStream_t st);
 

@@ -231,7 +231,7 @@ extern "C" sp2_status sp2_density_matrix_noalloc(const float* H, int N, int N_oc
   const int rgrid = (N + 7) / 8 < 2 * ds.num_sms ? (N + 7) / 8 : 2 * ds.num_sms;
   NA_CK(launch_gershgorin(H, N, N, (long long)N * N, 1, part, &sm->tickets[0], ctl, nullptr, ggrid, st));
   NA_CK(launch_input_layer(reinterpret_cast<const float* const*>(&sm->H), &sm->N, N, D_out, N, (long long)N * N,
-                           hi[0], lo[0], ld_h, slot_h, N, (int)ld_h, lo_scale, ctl, nullptr, part, &sm->tickets[0], 1,
+                           hi[0], lo[0], nullptr, ld_h, slot_h, N, (int)ld_h, lo_scale, ctl, nullptr, part, &sm->tickets[0], 1,
                            1, 1, igrid, st));
   NA_CK(launch_rownorm(D_out, N, (long long)N * N, &sm->N, 1, N, rn, N, ctl, part, &sm->tickets[0], rgrid, st));
 

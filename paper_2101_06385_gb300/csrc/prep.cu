@@ -177,7 +177,8 @@ __global__ void __launch_bounds__(256) input_layer_kernel(const float* const* __
                                                           const int* __restrict__ Ns, long long ld_in_fixed,
                                                           float* __restrict__ Y, long long ld_y, long long slot_y,
                                                           __half* __restrict__ hi, __half* __restrict__ lo,
-                                                          long long ld_h, long long slot_h, int rows_pad, int cols_pad,
+                                                          __half* __restrict__ hp, long long ld_h, long long slot_h,
+                                                          int rows_pad, int cols_pad,
                                                           float lo_scale,
                                                           Ctl* __restrict__ ctl, const double* __restrict__ bounds,
                                                           double2* __restrict__ partials, unsigned* __restrict__ tickets,
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(256) input_layer_kernel(const float* const* __
       float* yrow = Y + (long long)b * slot_y + (long long)r * ld_y;
       __half* hirow = hi ? hi + (long long)b * slot_h + (long long)r * ld_h : nullptr;
       __half* lorow = (hi && lo) ? lo + (long long)b * slot_h + (long long)r * ld_h : nullptr;
+      __half* hprow = (hi && hp) ? hp + (long long)b * slot_h + (long long)r * ld_h : nullptr;
       float sqf = 0.f;
       for (int col = threadIdx.x; col < cols; col += blockDim.x) {
         float y = 0.f;
@@ -224,6 +226,7 @@ __global__ void __launch_bounds__(256) input_layer_kernel(const float* const* __
           split_fp16(y, lo_scale, h16, l16);
           hirow[col] = h16;
           if (lorow) lorow[col] = l16;
+          if (hprow) hprow[col] = __float2half_rn(__half2float(h16) * lo_scale);
         }
       }
       sq += (double)sqf;
@@ -360,20 +363,22 @@ __global__ void split_kernel(const float* __restrict__ X, long long n, float lo_
 // ---------------------------------------------------------------- split, padded
 // X [B][N][ld_x] FP32 -> hi/lo [B][N][ld_h] FP16 with the row tail [N, ld_h) zeroed.
 __global__ void split_pad_kernel(const float* __restrict__ X, long long ld_x, long long slot_x, int N, int B,
-                                 float lo_scale, __half* __restrict__ hi, __half* __restrict__ lo, long long ld_h,
-                                 long long slot_h) {
+                                 float lo_scale, __half* __restrict__ hi, __half* __restrict__ lo,
+                                 __half* __restrict__ hp, long long ld_h, long long slot_h) {
   const long long rows = (long long)N * B;
   for (long long gr = blockIdx.x; gr < rows; gr += gridDim.x) {
     const int b = (int)(gr / N), r = (int)(gr % N);
     const float* xr = X + (long long)b * slot_x + (long long)r * ld_x;
     __half* hr = hi + (long long)b * slot_h + (long long)r * ld_h;
     __half* lr = lo ? lo + (long long)b * slot_h + (long long)r * ld_h : nullptr;
+    __half* pr = hp ? hp + (long long)b * slot_h + (long long)r * ld_h : nullptr;
     for (int c = threadIdx.x; c < (int)ld_h; c += blockDim.x) {
       const float x = (c < N) ? xr[c] : 0.f;
       __half h, l;
       split_fp16(x, lo_scale, h, l);
       hr[c] = h;
       if (lr) lr[c] = l;
+      if (pr) pr[c] = __float2half_rn(__half2float(h) * lo_scale);
     }
   }
 }
@@ -440,11 +445,11 @@ cudaError_t launch_gershgorin_batched(const float* const* Hs, const int* Ns, Ctl
 }
 
 cudaError_t launch_input_layer(const float* const* Hs, const int* Ns, long long ld_in, float* Y, long long ld_y,
-                               long long slot_y, __half* hi, __half* lo, long long ld_h, long long slot_h, int rows_pad,
-                               int cols_pad, float lo_scale, Ctl* ctl, const double* bounds, double2* partials, unsigned* tickets,
+                               long long slot_y, __half* hi, __half* lo, __half* hp, long long ld_h, long long slot_h,
+                               int rows_pad, int cols_pad, float lo_scale, Ctl* ctl, const double* bounds, double2* partials, unsigned* tickets,
                                int shift, int ctl_step, int batch, int grid_x, cudaStream_t st) {
   dim3 grid(grid_x, batch);
-  input_layer_kernel<<<grid, 256, 0, st>>>(Hs, Ns, ld_in, Y, ld_y, slot_y, hi, lo, ld_h, slot_h, rows_pad, cols_pad,
+  input_layer_kernel<<<grid, 256, 0, st>>>(Hs, Ns, ld_in, Y, ld_y, slot_y, hi, lo, hp, ld_h, slot_h, rows_pad, cols_pad,
                                            lo_scale, ctl,
                                            bounds, partials, tickets, shift, ctl_step);
   return cudaGetLastError();
@@ -466,8 +471,9 @@ cudaError_t launch_split(const float* X, long long n, float lo_scale, __half* hi
 }
 
 cudaError_t launch_split_pad(const float* X, long long ld_x, long long slot_x, int N, int B, float lo_scale,
-                             __half* hi, __half* lo, long long ld_h, long long slot_h, int grid, cudaStream_t st) {
-  split_pad_kernel<<<grid, 256, 0, st>>>(X, ld_x, slot_x, N, B, lo_scale, hi, lo, ld_h, slot_h);
+                             __half* hi, __half* lo, __half* hp, long long ld_h, long long slot_h, int grid,
+                             cudaStream_t st) {
+  split_pad_kernel<<<grid, 256, 0, st>>>(X, ld_x, slot_x, N, B, lo_scale, hi, lo, hp, ld_h, slot_h);
   return cudaGetLastError();
 }
 
