@@ -58,6 +58,8 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU sample")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-SP2 measurement")
+    ap.add_argument("--no-network", action="store_true", help="skip the network forward/backward measurement")
     return ap.parse_args()
 
 
@@ -222,6 +224,65 @@ def run_reference(args):
     return 0
 
 
+def _bench_batched(sp2, sp2_inputs, dev, reps=3):
+    """512 Hamiltonians, N uniform in {64..1024} step 32, gaps U[0.05, 0.3]."""
+    import torch
+
+    cfg = sp2_inputs.batched_config()
+    Hs = [torch.from_numpy(sp2_inputs.batched_instance(N, n, g, s).h32()).to(dev) for (N, n, g, s) in cfg]
+    n_occ = [c[1] for c in cfg]
+    sp2.density_matrix_batched(Hs, n_occ)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        _, st = sp2.density_matrix_batched(Hs, n_occ)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    layers = [s.iterations + 2 for s in st]
+    flops = sum(l * 2.0 * c[0] ** 3 for l, c in zip(layers, cfg))
+    alg = sum(l * 3.0 * c[0] ** 3 for l, c in zip(layers, cfg))
+    return {"instances": len(cfg), "ms": ms, "tflops_2n3": flops / (ms * 1e-3) / 1e12,
+            "tflops_split_alg_3n3": alg / (ms * 1e-3) / 1e12, "layers_min": min(layers),
+            "layers_mean": float(np.mean(layers)), "layers_max": max(layers),
+            "all_converged": all(s.status == 0 for s in st)}
+
+
+def _bench_network(sp2, sp2_inputs, dev, B=64, N=2048, L=20, ckpt_every=5, reps=2):
+    """Differentiable network: 64 gapped Hamiltonians of N = 2048, 20 layers,
+    coefficients initialised to the SP2 branch values of instance 0."""
+    import torch
+
+    Hs = [sp2_inputs.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), 2000 + i, device=str(dev)).h32()
+          for i in range(B)]
+    H = torch.from_numpy(np.stack(Hs)).to(dev)
+    _, st = sp2.density_matrix(H[0].contiguous(), N // 2, precision="split")
+    sig = st.sigmas + [1 if k % 2 == 0 else -1 for k in range(L)]
+    coef = torch.tensor([[1.0, 0.0, 0.0] if s > 0 else [-1.0, 2.0, 0.0] for s in sig[:L]], dtype=torch.float32)
+    X, ck, _ = sp2.network_forward(H, coef, ckpt_every)
+    G = torch.randn_like(X) * 1e-3
+    G = 0.5 * (G + G.transpose(1, 2))
+    sp2.network_backward(H, coef, ckpt_every, ck, G.contiguous())
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    for _ in range(reps):
+        X, ck, _ = sp2.network_forward(H, coef, ckpt_every)
+    ev[1].record()
+    for _ in range(reps):
+        sp2.network_backward(H, coef, ckpt_every, ck, G.contiguous())
+    ev[2].record()
+    torch.cuda.synchronize(dev)
+    fwd = ev[0].elapsed_time(ev[1]) / reps
+    bwd = ev[1].elapsed_time(ev[2]) / reps
+    f_fwd = B * L * 3.0 * N ** 3
+    # backward: recomputation of the non-checkpointed layers + the split SYR2K (6 N^3 per layer)
+    f_bwd = B * (L - (L + ckpt_every - 1) // ckpt_every) * 3.0 * N ** 3 + B * L * 6.0 * N ** 3
+    return {"B": B, "N": N, "layers": L, "ckpt_every": ckpt_every, "forward_ms": fwd, "backward_ms": bwd,
+            "forward_tflops_alg": f_fwd / (fwd * 1e-3) / 1e12, "backward_tflops_alg": f_bwd / (bwd * 1e-3) / 1e12}
+
+
 def run_ours(args):
     import torch
 
@@ -277,8 +338,9 @@ def run_ours(args):
     value = flops_eff * ws / (ms * 1e-3) / 1e12
 
     # squaring kernel: active launches of the timed steps
-    act = [x for s in stats for x in s.layer_ms[: s.iterations + 2]]
-    idle = [x for s in stats for x in s.layer_ms[s.iterations + 2:]]
+    act = [x for s in stats for x in s.square_ms[: s.iterations + 2]]
+    idle = [x for s in stats for x in s.square_ms[s.iterations + 2:]]
+    rown = [x - y for s in stats for x, y in zip(s.layer_ms[: s.iterations + 2], s.square_ms[: s.iterations + 2])]
     launch_ms = statistics.mean(act)
     alg_flops = 3.0 * N ** 3
     peaks, src = _peaks()
@@ -352,6 +414,9 @@ def run_ours(args):
                          f"{dt:.1f} s; full solve would be ~{layers} layers x {N // rows} blocks"}
         del S0, H64
 
+    batched = None if args.no_batched else _bench_batched(sp2, sp2_inputs, dev)
+    network = None if args.no_network else _bench_network(sp2, sp2_inputs, dev)
+
     launches_per_step = 2 + st.launches
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
@@ -378,9 +443,12 @@ def run_ours(args):
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{src} bf16_tflops_sustained (FP16 dense = BF16 dense rate)",
-                     "kernel": "syrk_tc_kernel<split>", "launch_ms_mean": launch_ms,
+                     "kernel": "syrk_tc1_kernel<split>", "launch_ms_mean": launch_ms,
                      "idle_launch_ms_mean": statistics.mean(idle) if idle else None,
+                     "rownorm_ms_mean": statistics.mean(rown) if rown else None,
                      "executed_tflops": exec_flops / (launch_ms * 1e-3) / 1e12},
+        "batched": batched,
+        "network": network,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": int(launches_per_step * args.steps),

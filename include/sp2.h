@@ -94,8 +94,10 @@ typedef struct {
                                      iterations + 2 find the solve finished and return at once */
   int8_t sigma[SP2_MAX_LAYERS];   /* sigma[k] = sigma_{k+1} in {+1,-1}; 0 past the end */
   double iderr[SP2_MAX_LAYERS];   /* iderr[k] = IdErr_{k+1} */
-  float layer_ms[SP2_MAX_LAYERS]; /* device time of squaring launch k (k < launches): the loop
-                                     layers, then the two refinement layers of Eq. 15 */
+  float layer_ms[SP2_MAX_LAYERS]; /* device time of layer k (k < launches): squaring launch plus
+                                     its row-norm pass; the loop layers, then the two refinement
+                                     layers of Eq. 15 */
+  float square_ms[SP2_MAX_LAYERS];/* device time of squaring launch k alone */
 } sp2_stats;
 
 /* Library set-up.  cfg == NULL selects the defaults {device 0, NULL stream,

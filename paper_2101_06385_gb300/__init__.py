@@ -89,6 +89,7 @@ class _Stats(ctypes.Structure):
         ("sigma", ctypes.c_int8 * SP2_MAX_LAYERS),
         ("iderr", ctypes.c_double * SP2_MAX_LAYERS),
         ("layer_ms", ctypes.c_float * SP2_MAX_LAYERS),
+        ("square_ms", ctypes.c_float * SP2_MAX_LAYERS),
     ]
 
 
@@ -109,6 +110,7 @@ class Stats:
     prologue_ms: float = 0.0
     launches: int = 0
     layer_ms: List[float] = dataclasses.field(default_factory=list)
+    square_ms: List[float] = dataclasses.field(default_factory=list)
 
     @property
     def converged(self) -> bool:
@@ -204,7 +206,8 @@ def _stats(s: _Stats, status: int) -> Stats:
                  e_min=s.e_min, e_max=s.e_max, idemp_err=s.idemp_err, trace=s.trace, alpha=s.alpha,
                  time_ms=s.time_ms, flops_alg=s.flops_alg, sigmas=[int(v) for v in s.sigma[:n]],
                  iderr=[float(v) for v in s.iderr[:n]], prologue_ms=s.prologue_ms, launches=s.launches,
-                 layer_ms=[float(v) for v in s.layer_ms[:s.launches]])
+                 layer_ms=[float(v) for v in s.layer_ms[:s.launches]],
+                 square_ms=[float(v) for v in s.square_ms[:s.launches]])
 
 
 def density_matrix(H: torch.Tensor, n_occ: int, tol: float = 0.0, max_iter: int = 100,

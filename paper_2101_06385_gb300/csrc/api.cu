@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstddef>
 #include <cstring>
@@ -82,9 +83,13 @@ struct State {
   size_t stage_bytes = 0;
   cudaEvent_t stage_done = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  cudaEvent_t lev[SP2_MAX_LAYERS + 1] = {};  // around each squaring launch
+  cudaEvent_t lev[SP2_MAX_LAYERS + 1] = {};  // around each layer (squaring + row norms)
+  cudaEvent_t lsq[SP2_MAX_LAYERS] = {};      // after each squaring launch
   // cached tile list
   int tiles_key_N = -1, tiles_key_B = -1, tiles_key_kind = -1;
+  // squaring kernel of the single-matrix solve: CTA pairs sharing B through
+  // TMA multicast (default) or single CTAs (SP2_SQUARE_KERNEL=single)
+  bool pair_kernel = true;
 };
 
 State g;
@@ -135,7 +140,10 @@ inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m
 // Upper-triangle tile list in grouped order: groups of 8 x 8 block tiles
 // are visited upper-triangle first, block tiles row-major inside a group, so
 // that the CTAs running at the same time share row panels in L2.
-void build_tiles(int N, int B, int tile, bool halves, std::vector<uint32_t>& out, int& per_instance) {
+// halves: 0 = one tile per block (FFMA kernel), 1 = both 128-row halves of a
+// 256 x 256 super tile unless the second lies past N, 2 = both halves always
+// (adjacent; the CTA-pair kernel takes them together).
+void build_tiles(int N, int B, int tile, int halves, std::vector<uint32_t>& out, int& per_instance) {
   const int T = (N + tile - 1) / tile;
   const int G = 8;
   std::vector<uint32_t> one;
@@ -145,7 +153,7 @@ void build_tiles(int N, int B, int tile, bool halves, std::vector<uint32_t>& out
         for (int J = std::max(I, gj); J < std::min(gj + G, T); ++J) {
           if (halves) {
             one.push_back(pack_tile(0, I, J, 0));
-            if (I * tile + tile / 2 < N) one.push_back(pack_tile(0, I, J, 1));
+            if (halves == 2 || I * tile + tile / 2 < N) one.push_back(pack_tile(0, I, J, 1));
           } else {
             one.push_back(pack_tile(0, I, J, 0));
           }
@@ -159,11 +167,12 @@ void build_tiles(int N, int B, int tile, bool halves, std::vector<uint32_t>& out
 
 bool tc_precision(int p) { return p == SP2_PREC_SPLIT_FP16 || p == SP2_PREC_FP16; }
 
-// Uploads a uniform-size tile list (B instances of size N).
-sp2_status upload_tiles(int N, int B, bool tc, int* ntiles_out) {
+// Uploads a uniform-size tile list (B instances of size N); kind 0 = FFMA
+// tiles, 1 = tensor-core halves, 2 = tensor-core super-tile pairs.
+sp2_status upload_tiles(int N, int B, int kind, int* ntiles_out) {
   std::vector<uint32_t> tiles;
   int per = 0;
-  build_tiles(N, B, tc ? kTcBN : kSimtB, tc, tiles, per);
+  build_tiles(N, B, kind ? kTcBN : kSimtB, kind, tiles, per);
   const int nt = (int)tiles.size();
   void *dt, *doff, *dcnt, *dpart, *ddone;
   CKS(ws(B_TILES, nt * sizeof(uint32_t), &dt));
@@ -171,7 +180,6 @@ sp2_status upload_tiles(int N, int B, bool tc, int* ntiles_out) {
   CKS(ws(B_TCNT, B * sizeof(int), &dcnt));
   CKS(ws(B_TPART, nt * sizeof(double2), &dpart));
   CKS(ws(B_IDONE, B * sizeof(unsigned), &ddone, true));
-  const int kind = tc ? 1 : 0;
   if (!(g.tiles_key_N == N && g.tiles_key_B == B && g.tiles_key_kind == kind)) {
     size_t bytes = nt * sizeof(uint32_t) + 2 * B * sizeof(int);
     void* h;
@@ -235,14 +243,14 @@ sp2_status tmaps_for(const void* hi, const void* lo, int N, int B, long long ld_
 // Tensor maps {hp(A box), lo(A box), hi(A box), hi(B box), lo(B box)} for the
 // single-accumulator squaring kernel (hp, lo may be null for plain FP16).
 sp2_status tmaps5_for(const void* hp, const void* lo, const void* hi, int N, int B, long long ld_h, long long slot_h,
-                      CUtensorMap* m) {
+                      CUtensorMap* m, int box_b = kTcBN) {
   const void* hp_ = hp ? hp : hi;
   const void* lo_ = lo ? lo : hi;
   bool ok = make_tmap_f16(&m[0], hp_, N, N, B, ld_h, slot_h, 32, kTcBM) &&
             make_tmap_f16(&m[1], lo_, N, N, B, ld_h, slot_h, 32, kTcBM) &&
             make_tmap_f16(&m[2], hi, N, N, B, ld_h, slot_h, 32, kTcBM) &&
-            make_tmap_f16(&m[3], hi, N, N, B, ld_h, slot_h, 32, kTcBN) &&
-            make_tmap_f16(&m[4], lo_, N, N, B, ld_h, slot_h, 32, kTcBN);
+            make_tmap_f16(&m[3], hi, N, N, B, ld_h, slot_h, 32, box_b) &&
+            make_tmap_f16(&m[4], lo_, N, N, B, ld_h, slot_h, 32, box_b);
   if (!ok) {
     set_err("cuTensorMapEncodeTiled failed (N=%d, ld=%lld)", N, ld_h);
     return SP2_ERR_CUDA;
@@ -352,6 +360,11 @@ sp2_status sp2_init(const sp2_config* cfg) {
     CK(cudaEventCreate(&g.ev0));
     CK(cudaEventCreate(&g.ev1));
     for (int i = 0; i <= SP2_MAX_LAYERS; ++i) CK(cudaEventCreate(&g.lev[i]));
+    for (int i = 0; i < SP2_MAX_LAYERS; ++i) CK(cudaEventCreate(&g.lsq[i]));
+  }
+  {
+    const char* kv = getenv("SP2_SQUARE_KERNEL");
+    g.pair_kernel = !(kv && strcmp(kv, "single") == 0);
   }
   g.device = c.device;
   g.stream = (cudaStream_t)c.stream;
@@ -381,6 +394,8 @@ sp2_status sp2_finalize(void) {
   for (int i = 0; i <= SP2_MAX_LAYERS; ++i) {
     if (g.lev[i]) cudaEventDestroy(g.lev[i]);
     g.lev[i] = nullptr;
+    if (i < SP2_MAX_LAYERS && g.lsq[i]) cudaEventDestroy(g.lsq[i]);
+    if (i < SP2_MAX_LAYERS) g.lsq[i] = nullptr;
   }
   g.tiles_key_N = -1;
   g.init = false;
@@ -470,7 +485,7 @@ sp2_status sp2_layer(const float* X, int B, int N, float a, float b, float c, fl
   const bool tc = tc_precision(g.precision);
   const bool split = g.precision == SP2_PREC_SPLIT_FP16;
   int ntiles = 0;
-  CKS(upload_tiles(N, B, tc, &ntiles));
+  CKS(upload_tiles(N, B, tc ? 1 : 0, &ntiles));
   void *ns, *params, *traces, *err, *dptr;
   CKS(ws(B_NS, B * sizeof(int), &ns));
   CKS(ws(B_PARAMS, sizeof(LayerParams), &params));
@@ -576,7 +591,7 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
   cudaStream_t st = g.stream;
 
   int ntiles = 0;
-  CKS(upload_tiles(N, 1, tc, &ntiles));
+  CKS(upload_tiles(N, 1, tc ? (g.pair_kernel ? 2 : 1) : 0, &ntiles));
   void *ctl, *ns, *hs, *dptr, *err, *part, *tick;
   CKS(ws(B_CTL, sizeof(Ctl), &ctl));
   CKS(ws(B_NS, sizeof(int), &ns));
@@ -651,22 +666,27 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
     CK(launch_rownorm(D_out, N, (long long)N * N, (const int*)ns, 1, N, (double*)rn, N, (Ctl*)ctl, (double2*)part,
                       (unsigned*)tick, rgrid, st));
     CUtensorMap m[2][5];
-    CKS(tmaps5_for(hp[0], lo[0], hi[0], N, 1, ld_h, slot_h, m[0]));
-    CKS(tmaps5_for(hp[1], lo[1], hi[1], N, 1, ld_h, slot_h, m[1]));
+    const int boxb = g.pair_kernel ? kTcBM : kTcBN;
+    CKS(tmaps5_for(hp[0], lo[0], hi[0], N, 1, ld_h, slot_h, m[0], boxb));
+    CKS(tmaps5_for(hp[1], lo[1], hi[1], N, 1, ld_h, slot_h, m[1], boxb));
     A.Yin = D_out;
     A.Yout = D_out;
     A.ld_y = N;
     A.slot_y = (long long)N * N;
     A.ld_h = ld_h;
     A.slot_h = slot_h;
-    const int grid = std::min(ntiles, g.num_sms);
+    const int grid = std::min(ntiles, g.num_sms) & (g.pair_kernel ? ~1 : ~0);
     CK(cudaEventRecord(g.lev[0], st));
     for (int k = 0; k < max_iter + 2; ++k) {
       const int cur = k & 1;
       A.hi_out = (__half*)hi[cur ^ 1];
       A.lo_out = (__half*)lo[cur ^ 1];
       A.hp_out = (__half*)hp[cur ^ 1];
-      CK(launch_syrk_tc1(A, m[cur], split, grid, st));
+      if (g.pair_kernel)
+        CK(launch_syrk_tc2(A, m[cur], split, grid, st));
+      else
+        CK(launch_syrk_tc1(A, m[cur], split, grid, st));
+      CK(cudaEventRecord(g.lsq[k], st));
       CK(launch_rownorm(D_out, N, (long long)N * N, (const int*)ns, 1, N, (double*)rn, N, (Ctl*)ctl, (double2*)part,
                         (unsigned*)tick, rgrid, st));
       CK(cudaEventRecord(g.lev[k + 1], st));
@@ -689,6 +709,7 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
       A.Yin = (float*)Y[cur];
       A.Yout = (float*)Y[cur ^ 1];
       CK(launch_syrk_simt(A, ntiles, st));
+      CK(cudaEventRecord(g.lsq[k], st));
       CK(launch_rownorm((float*)Y[cur ^ 1], ld_y, slot_y, (const int*)ns, 1, N, (double*)rn, N, (Ctl*)ctl,
                         (double2*)part, (unsigned*)tick, rgrid, st));
       CK(cudaEventRecord(g.lev[k + 1], st));
@@ -712,9 +733,11 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
   CK(cudaEventElapsedTime(&pm, g.ev0, g.lev[0]));
   stats->prologue_ms = pm;
   for (int k = 0; k < max_iter + 2; ++k) {
-    float lm = 0.f;
+    float lm = 0.f, sm = 0.f;
     CK(cudaEventElapsedTime(&lm, g.lev[k], g.lev[k + 1]));
+    CK(cudaEventElapsedTime(&sm, g.lev[k], g.lsq[k]));
     stats->layer_ms[k] = lm;
+    stats->square_ms[k] = sm;
   }
   return status_of(c, e);
 }
@@ -753,7 +776,7 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   for (int b : order) {
     std::vector<uint32_t> one;
     int per = 0;
-    build_tiles(N[b], 1, tile, tc, one, per);
+    build_tiles(N[b], 1, tile, tc ? 1 : 0, one, per);
     toff[b] = (int)tiles.size();
     tcnt[b] = per;
     for (uint32_t t : one) tiles.push_back(t | ((uint32_t)b << 20));
@@ -1029,7 +1052,7 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
     CK(cudaMemcpy2DAsync(bounds, 2 * sizeof(double), (char*)ctl + offsetof(Ctl, e_min), sizeof(Ctl),
                          2 * sizeof(double), B, cudaMemcpyDeviceToDevice, st));
   int ntiles = 0;
-  CKS(upload_tiles(N, B, tc, &ntiles));
+  CKS(upload_tiles(N, B, tc ? 1 : 0, &ntiles));
   void *params, *alpha, *rn, *part, *tick, *err;
   CKS(ws(B_PARAMS, plan.params.size() * sizeof(LayerParams), &params));
   CKS(ws(B_BOUNDS, plan.alpha.size() * sizeof(double), &alpha));
@@ -1181,7 +1204,7 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
       plan.params[(size_t)n * B + b].alpha_out = 0.0;
     }
   int ntiles = 0;
-  CKS(upload_tiles(N, B, true, &ntiles));
+  CKS(upload_tiles(N, B, 1, &ntiles));
   const long long ld_h = round_up(N, 64), slot_h = ld_h * N;
   void *params, *params2, *nal, *rn, *err, *seg, *yh, *yl = nullptr, *gh[2], *gl[2] = {nullptr, nullptr}, *dots,
        *tdots;

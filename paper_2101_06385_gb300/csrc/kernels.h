@@ -85,6 +85,11 @@ cudaError_t launch_rownorm(const float* Y, long long ld_y, long long slot_y, con
 // hi(B), lo(B)}; split = false: plain FP16, tmaps[2] = hi(A), tmaps[3] = hi(B).
 cudaError_t launch_syrk_tc1(const SqArgs& a, const CUtensorMap* tmaps, bool split, int grid, cudaStream_t st);
 size_t syrk_tc1_smem_bytes(bool split);
+// The same kernel run by CTA pairs (clusters of 2) that share the B operand by
+// TMA multicast: tiles come in (h = 0, h = 1) pairs of one super tile,
+// a.ntiles = 2 x super tiles, and the B maps have 128-row boxes.
+cudaError_t launch_syrk_tc2(const SqArgs& a, const CUtensorMap* tmaps, bool split, int grid, cudaStream_t st);
+size_t syrk_tc2_smem_bytes(bool split);
 
 cudaError_t launch_syrk_simt(const SqArgs& a, int grid, cudaStream_t st);
 

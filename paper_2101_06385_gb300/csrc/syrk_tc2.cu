@@ -1,0 +1,484 @@
+// Single-accumulator split-FP16 squaring on tcgen05 with a double-buffered
+// TMEM accumulator, run by CTA pairs that share the B operand through TMA
+// multicast (sm_103a).
+//
+// The two 128-row halves (h = 0, 1) of an upper 256 x 256 super tile need the
+// same 256 B rows.  A cluster of two CTAs takes both halves of one super tile;
+// each CTA loads its own 128 A rows and one 128-row half of B, and the B half
+// is multicast into both CTAs' shared memory, so B is read from L2 once per
+// super tile instead of twice.  A stage may be refilled only when both CTAs'
+// MMAs have released it (the release is a multicast commit).
+//
+// Alg. 2 / Eq. 14 with the low part scaled (Eq. 12, lo' = 2^s (Y - hi)):
+//     2^s P = hp hi + lo' hi + hi lo',     hp = 2^s hi (exact in FP16),
+// so all three products accumulate into ONE FP32 TMEM accumulator of
+// 128 x 256 (256 columns).  Two such accumulators fit in the 512 TMEM
+// columns: while the epilogue warps drain tile t from one, the MMA issuer
+// fills the other with tile t+1, and the epilogue (FP32 update, re-split,
+// row and mirrored stores, traces) runs under the next tile's MMAs.
+//
+// CTA = 10 warps, persistent over the upper-tile list (one CTA per SM):
+//   warp 0      TMA producer (one thread): hp, lo', hi of the 128 A rows and
+//               hi, lo' of the 256 B rows per 32-wide K stage (56 KB, 4 stages)
+//   warp 1      TMEM allocation + MMA issuer (one thread)
+//   warps 2..9  epilogue: TMEM lane quarter (warp % 4) x column half
+// Plain FP16 (split = false): hi hi only, 24 KB stages, 8 stages.
+// Every mbarrier wait is bounded; see syrk_tc.cu for the time-out path.
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_ptx.cuh"
+#include "tile_finish.cuh"
+
+namespace sp2 {
+namespace tc2 {
+
+using namespace sp2::tc;
+
+constexpr int STAGE_SPLIT = 3 * A_BYTES + 2 * B_BYTES;  // 56 KB: hpA loA hiA hiB loB
+constexpr int STAGE_PLAIN = A_BYTES + B_BYTES;          // 24 KB: hiA hiB
+constexpr int STAGES_SPLIT = 4;
+constexpr int STAGES_PLAIN = 8;
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr uint32_t TMEM_COLS = 512;  // two 256-column accumulators
+
+// stage offsets (split): hpA 0, loA 8K, hiA 16K, hiB 24K, loB 40K
+constexpr int OFF_HPA = 0, OFF_LOA = A_BYTES, OFF_HIA = 2 * A_BYTES, OFF_HIB = 3 * A_BYTES,
+              OFF_LOB = 3 * A_BYTES + B_BYTES;
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive;\n\tbarrier.cluster.wait;" ::: "memory");
+}
+
+// TMA load multicast to the CTAs in mask: same shared offset in each, each
+// destination CTA's mbarrier at that offset receives the byte count.
+__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, uint64_t* bar,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
+      "[%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+// Arrive on the mbarrier at this offset in every CTA of mask once all prior
+// tcgen05 operations of this thread have completed.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                   smem_u32(bar)),
+               "h"(mask)
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(THREADS, 1)
+    syrk_tc2_kernel(const __grid_constant__ CUtensorMap tm_hpA, const __grid_constant__ CUtensorMap tm_loA,
+                    const __grid_constant__ CUtensorMap tm_hiA, const __grid_constant__ CUtensorMap tm_hiB,
+                    const __grid_constant__ CUtensorMap tm_loB, const SqArgs a) {
+  constexpr int STAGES = SPLIT ? STAGES_SPLIT : STAGES_PLAIN;
+  constexpr int STAGE_BYTES = SPLIT ? STAGE_SPLIT : STAGE_PLAIN;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tmem_full = empty + STAGES;   // [2]
+  uint64_t* tmem_empty = tmem_full + 2;   // [2]
+  uint64_t* drain = tmem_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  __shared__ int s_abort;
+  __shared__ double s_red[EPI_WARPS][2];
+  __shared__ int s_got[EPI_WARPS];
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 2);  // released by both CTAs' MMAs
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tmem_full[i], 1);
+      mbar_init(&tmem_empty[i], EPI_WARPS);
+    }
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  // the peer's barriers must exist before any multicast reaches them
+  cluster_sync();
+  const uint32_t tmem_base = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+  const int rank = (int)cluster_rank();
+  const int cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int nsuper = a.ntiles >> 1;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      uint32_t armed[STAGES];
+#pragma unroll
+      for (int s = 0; s < STAGES; ++s) armed[s] = 0;
+      for (int u = cl; u < nsuper && ok; u += ncl) {
+        const int t = 2 * u + rank;
+        int b, I, J, h;
+        unpack_tile(a.tiles[t], b, I, J, h);
+        if (!load_params(a, b).active) continue;
+        const int N = a.Ns[b];
+        const int rowA = I * BN + h * BM, rowB = J * BN + rank * BM;
+        const int nk = (N + BK - 1) / BK;
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + stage * STAGE_BYTES;
+          mbar_expect_tx(&full[stage], STAGE_BYTES);
+          const int k0 = kb * BK;
+          if (SPLIT) {
+            tma_load_3d(st + OFF_HPA, &tm_hpA, k0, rowA, b, &full[stage]);
+            tma_load_3d(st + OFF_LOA, &tm_loA, k0, rowA, b, &full[stage]);
+            tma_load_3d(st + OFF_HIA, &tm_hiA, k0, rowA, b, &full[stage]);
+            tma_load_3d_mc(st + OFF_HIB + rank * (B_BYTES / 2), &tm_hiB, k0, rowB, b, &full[stage], 0x3);
+            tma_load_3d_mc(st + OFF_LOB + rank * (B_BYTES / 2), &tm_loB, k0, rowB, b, &full[stage], 0x3);
+          } else {
+            tma_load_3d(st, &tm_hiA, k0, rowA, b, &full[stage]);
+            tma_load_3d_mc(st + A_BYTES + rank * (B_BYTES / 2), &tm_hiB, k0, rowB, b, &full[stage], 0x3);
+          }
+          ++armed[stage];
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok || *abort_flag) {
+        atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
+        for (int s = 0; s < STAGES; ++s) {
+          if (armed[s] == 0) continue;
+          const uint64_t t0 = globaltimer();
+          while (!mbar_try_wait(&full[s], (armed[s] - 1u) & 1u) && globaltimer() - t0 < kTimeoutNs) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, it = 0;
+      bool ok = true, issued = false;
+      for (int u = cl; u < nsuper && ok; u += ncl) {
+        const int t = 2 * u + rank;
+        int b, I, J, h;
+        unpack_tile(a.tiles[t], b, I, J, h);
+        if (!load_params(a, b).active) continue;
+        const int N = a.Ns[b];
+        const int nk = (N + BK - 1) / BK;
+        const uint32_t buf = it & 1u;
+        // the k-th use of a buffer waits for the epilogue's (k-1)-th release
+        if (!mbar_wait(&tmem_empty[buf], ((it >> 1) & 1u) ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem_base + buf * BN;
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!mbar_wait(&full[stage], phase, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + stage * STAGE_BYTES);
+#pragma unroll
+          for (int ks = 0; ks < BK / UMMA_K; ++ks) {
+            const uint32_t koff = ks * UMMA_K * 2;
+            const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
+            if (SPLIT) {
+              const uint64_t dhiB = make_desc_sw64(st + OFF_HIB + koff);
+              mma_f16(d, make_desc_sw64(st + OFF_HPA + koff), dhiB, acc);               // 2^s hi hi
+              mma_f16(d, make_desc_sw64(st + OFF_LOA + koff), dhiB, 1u);                // lo' hi
+              mma_f16(d, make_desc_sw64(st + OFF_HIA + koff), make_desc_sw64(st + OFF_LOB + koff), 1u);  // hi lo'
+            } else {
+              mma_f16(d, make_desc_sw64(st + koff), make_desc_sw64(st + A_BYTES + koff), acc);
+            }
+          }
+          mma_commit_mc(&empty[stage], 0x3);  // release the stage in both CTAs
+          issued = true;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        mma_commit(&tmem_full[buf]);
+        ++it;
+      }
+      if (!ok) atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
+      if (issued) {
+        mma_commit(drain);
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int ew = warp - 2;                 // 0..7
+    const int q = warp & 3;                  // TMEM lane quarter
+    const int hc = ew >> 2;                  // column half of the 256-wide tile
+    const int row_local = q * 32 + lane;
+    const float unscale = SPLIT ? a.lo_unscale : 1.f;
+    const float lo_scale = a.lo_scale;
+    uint32_t it = 0;
+    for (int u = cl; u < nsuper; u += ncl) {
+      const int t = 2 * u + rank;
+      int b, I, J, h;
+      unpack_tile(a.tiles[t], b, I, J, h);
+      const LayerParams p = load_params(a, b);
+      if (!p.active) continue;
+      const int N = a.Ns[b];
+      const int r = I * BN + h * BM + row_local;
+      const bool mirror = (I != J);
+      const bool outD = (p.out_mode == OUT_D);
+      const uint32_t buf = it & 1u;
+      const bool got = mbar_wait(&tmem_full[buf], (it >> 1) & 1u, abort_flag);
+      if (lane == 0) s_got[ew] = got ? 1 : 0;
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      int all = 1;
+#pragma unroll
+      for (int k = 0; k < EPI_WARPS; ++k) all &= s_got[k];
+      if (!all) {
+        if (!got && lane == 0) atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+
+      float* Y = a.Yout + (long long)b * a.slot_y;
+      const float* Yold = a.Yin + (long long)b * a.slot_y;
+      const long long ld = a.ld_y;
+      __half* ho = a.hi_out ? a.hi_out + (long long)b * a.slot_h : nullptr;
+      __half* lo_ = a.lo_out ? a.lo_out + (long long)b * a.slot_h : nullptr;
+      __half* hp_ = a.hp_out ? a.hp_out + (long long)b * a.slot_h : nullptr;
+      const long long ldh = a.ld_h;
+      float* D = outD ? a.Dptr[b] : nullptr;
+      double tr = 0.0, sq = 0.0;
+      const uint32_t taddr = tmem_base + buf * BN + ((uint32_t)(q * 32) << 16) + hc * 128;
+      const bool vec_y = (ld & 3) == 0;
+
+#pragma unroll 1
+      for (int ch = 0; ch < 4; ++ch) {
+        uint32_t v[32];
+        __syncwarp();
+        tmem_ld32(taddr + ch * 32, v);
+        tmem_ld_wait();
+        if (ch == 3) {
+          // accumulator drained: the MMA issuer may reuse this buffer
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tmem_empty[buf]);
+        }
+        const int c0 = J * BN + hc * 128 + ch * 32;
+        float y[32];
+        float ydiag = 0.f;
+        if (r < N) {
+          const bool full_chunk = (c0 + 32 <= N) && vec_y;
+          if (full_chunk) {
+            const float4* src = reinterpret_cast<const float4*>(Yold + (long long)r * ld + c0);
+#pragma unroll
+            for (int j4 = 0; j4 < 8; ++j4) {
+              const float4 o = src[j4];
+              y[4 * j4 + 0] = o.x;
+              y[4 * j4 + 1] = o.y;
+              y[4 * j4 + 2] = o.z;
+              y[4 * j4 + 3] = o.w;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) y[j] = (c0 + j < N) ? Yold[(long long)r * ld + c0 + j] : 0.f;
+          }
+          float sqf = 0.f;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float P = __uint_as_float(v[j]) * unscale;
+            float yn;
+            if (r == c0 + j) {
+              const double pd = a.rn ? a.rn[(long long)b * a.ld_rn + r] : (double)P;
+              const double yd = p.ca_d * (double)y[j] + p.cb_d * pd + p.cc_d;
+              tr += yd;
+              yn = (float)yd;
+              if (outD) ydiag = (float)(yd + p.alpha_out);
+            } else {
+              yn = fmaf(p.ca, y[j], p.cb * P);
+            }
+            if (c0 + j >= N) yn = 0.f;
+            y[j] = yn;
+            sqf = fmaf(yn, yn, sqf);
+          }
+          sq += (double)sqf;
+          if (outD) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (c0 + j < N) D[(long long)r * N + c0 + j] = (r == c0 + j) ? ydiag : y[j];
+          } else {
+            if (full_chunk) {
+              float4* dst = reinterpret_cast<float4*>(Y + (long long)r * ld + c0);
+#pragma unroll
+              for (int j4 = 0; j4 < 8; ++j4)
+                dst[j4] = make_float4(y[4 * j4], y[4 * j4 + 1], y[4 * j4 + 2], y[4 * j4 + 3]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (c0 + j < N) Y[(long long)r * ld + c0 + j] = y[j];
+            }
+            if (ho && c0 + 32 <= (int)ldh) {
+              // 32 halves per part, packed in registers; columns >= N carry zeros
+              uint32_t ph[16], pl[16], pp[16];
+#pragma unroll
+              for (int j2 = 0; j2 < 16; ++j2) {
+                __half h0, l0, h1, l1;
+                split_fp16(y[2 * j2], lo_scale, h0, l0);
+                split_fp16(y[2 * j2 + 1], lo_scale, h1, l1);
+                ph[j2] = pack_h2(h0, h1);
+                pl[j2] = pack_h2(l0, l1);
+                pp[j2] = pack_h2(__float2half_rn(__half2float(h0) * lo_scale),
+                                 __float2half_rn(__half2float(h1) * lo_scale));
+              }
+              uint4* dh = reinterpret_cast<uint4*>(ho + (long long)r * ldh + c0);
+#pragma unroll
+              for (int j4 = 0; j4 < 4; ++j4)
+                dh[j4] = make_uint4(ph[4 * j4], ph[4 * j4 + 1], ph[4 * j4 + 2], ph[4 * j4 + 3]);
+              if (lo_) {
+                uint4* dl = reinterpret_cast<uint4*>(lo_ + (long long)r * ldh + c0);
+#pragma unroll
+                for (int j4 = 0; j4 < 4; ++j4)
+                  dl[j4] = make_uint4(pl[4 * j4], pl[4 * j4 + 1], pl[4 * j4 + 2], pl[4 * j4 + 3]);
+              }
+              if (hp_) {
+                uint4* dp = reinterpret_cast<uint4*>(hp_ + (long long)r * ldh + c0);
+#pragma unroll
+                for (int j4 = 0; j4 < 4; ++j4)
+                  dp[j4] = make_uint4(pp[4 * j4], pp[4 * j4 + 1], pp[4 * j4 + 2], pp[4 * j4 + 3]);
+              }
+            }
+          }
+        }
+        // mirrored store: lanes hold consecutive rows r -> consecutive columns
+        if (mirror && r < N) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int c = c0 + j;
+            if (c < N) {
+              if (outD) {
+                D[(long long)c * N + r] = y[j];
+              } else {
+                Y[(long long)c * ld + r] = y[j];
+                if (ho) {
+                  __half hh, ll;
+                  split_fp16(y[j], lo_scale, hh, ll);
+                  ho[(long long)c * ldh + r] = hh;
+                  if (lo_) lo_[(long long)c * ldh + r] = ll;
+                  if (hp_) hp_[(long long)c * ldh + r] = __float2half_rn(__half2float(hh) * lo_scale);
+                }
+              }
+            }
+          }
+        }
+      }
+
+      if (mirror) sq *= 2.0;
+      tr = warp_sum_d(tr);
+      sq = warp_sum_d(sq);
+      if (lane == 0) {
+        s_red[ew][0] = tr;
+        s_red[ew][1] = sq;
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (ew == 0) {
+        double T = 0.0, Q = 0.0;
+        if (lane == 0)
+          for (int k = 0; k < EPI_WARPS; ++k) {
+            T += s_red[k][0];
+            Q += s_red[k][1];
+          }
+        finish_tile_warp(a, t, b, T, Q, p.out_mode);
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      ++it;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  // no CTA leaves while its peer may still multicast into it or arrive on it
+  cluster_sync();
+  if (warp == 1) {
+    __syncwarp();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
+}  // namespace tc2
+
+size_t syrk_tc2_smem_bytes(bool split) {
+  const int stages = split ? tc2::STAGES_SPLIT : tc2::STAGES_PLAIN;
+  const int sb = split ? tc2::STAGE_SPLIT : tc2::STAGE_PLAIN;
+  return (size_t)stages * sb + 1024 /* alignment slack */ + 256 /* barriers */;
+}
+
+cudaError_t launch_syrk_tc2(const SqArgs& a, const CUtensorMap* tm, bool split, int grid, cudaStream_t st) {
+  // grid: number of CTAs, even (two per cluster); a.ntiles = 2 x super tiles
+  const size_t smem = syrk_tc2_smem_bytes(split);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(grid & ~1), 1, 1);
+  cfg.blockDim = dim3(tc2::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e;
+  if (split) {
+    e = cudaFuncSetAttribute(tc2::syrk_tc2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<true>, tm[0], tm[1], tm[2], tm[3], tm[4], a);
+  } else {
+    e = cudaFuncSetAttribute(tc2::syrk_tc2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<false>, tm[0], tm[1], tm[2], tm[3], tm[4], a);
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace sp2
