@@ -217,7 +217,7 @@ bool make_tmap_f16(CUtensorMap* out, const void* base, int cols, int rows, int b
   cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g.encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -229,10 +229,10 @@ namespace {
 // instances with N x N used entries, row stride ld_h, slot stride slot_h.
 sp2_status tmaps_for(const void* hi, const void* lo, int N, int B, long long ld_h, long long slot_h, CUtensorMap* m) {
   const void* lo_ = lo ? lo : hi;
-  bool ok = make_tmap_f16(&m[0], hi, N, N, B, ld_h, slot_h, 32, kTcBM) &&
-            make_tmap_f16(&m[1], lo_, N, N, B, ld_h, slot_h, 32, kTcBM) &&
-            make_tmap_f16(&m[2], hi, N, N, B, ld_h, slot_h, 32, kTcBN) &&
-            make_tmap_f16(&m[3], lo_, N, N, B, ld_h, slot_h, 32, kTcBN);
+  bool ok = make_tmap_f16(&m[0], hi, N, N, B, ld_h, slot_h, 64, kTcBM) &&
+            make_tmap_f16(&m[1], lo_, N, N, B, ld_h, slot_h, 64, kTcBM) &&
+            make_tmap_f16(&m[2], hi, N, N, B, ld_h, slot_h, 64, kTcBN) &&
+            make_tmap_f16(&m[3], lo_, N, N, B, ld_h, slot_h, 64, kTcBN);
   if (!ok) {
     set_err("cuTensorMapEncodeTiled failed (N=%d, ld=%lld)", N, ld_h);
     return SP2_ERR_CUDA;
@@ -246,11 +246,11 @@ sp2_status tmaps5_for(const void* hp, const void* lo, const void* hi, int N, int
                       CUtensorMap* m, int box_b = kTcBN) {
   const void* hp_ = hp ? hp : hi;
   const void* lo_ = lo ? lo : hi;
-  bool ok = make_tmap_f16(&m[0], hp_, N, N, B, ld_h, slot_h, 32, kTcBM) &&
-            make_tmap_f16(&m[1], lo_, N, N, B, ld_h, slot_h, 32, kTcBM) &&
-            make_tmap_f16(&m[2], hi, N, N, B, ld_h, slot_h, 32, kTcBM) &&
-            make_tmap_f16(&m[3], hi, N, N, B, ld_h, slot_h, 32, box_b) &&
-            make_tmap_f16(&m[4], lo_, N, N, B, ld_h, slot_h, 32, box_b);
+  bool ok = make_tmap_f16(&m[0], hp_, N, N, B, ld_h, slot_h, 64, kTcBM) &&
+            make_tmap_f16(&m[1], lo_, N, N, B, ld_h, slot_h, 64, kTcBM) &&
+            make_tmap_f16(&m[2], hi, N, N, B, ld_h, slot_h, 64, kTcBM) &&
+            make_tmap_f16(&m[3], hi, N, N, B, ld_h, slot_h, 64, box_b) &&
+            make_tmap_f16(&m[4], lo_, N, N, B, ld_h, slot_h, 64, box_b);
   if (!ok) {
     set_err("cuTensorMapEncodeTiled failed (N=%d, ld=%lld)", N, ld_h);
     return SP2_ERR_CUDA;

@@ -138,10 +138,10 @@ void msg(const char* s) { set_error_text(s); }
 bool tmap(CUtensorMap* out, const void* base, int N, long long ld, int box_rows) {
   cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, 1};
   cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * N * 2};
-  cuuint32_t box[3] = {32, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   return g_encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

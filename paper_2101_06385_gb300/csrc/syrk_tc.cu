@@ -30,10 +30,10 @@ namespace sp2 {
 
 namespace tc {
 
-constexpr int STAGE_SPLIT = 2 * A_BYTES + 2 * B_BYTES;  // 48 KB: hiA loA hiB loB
-constexpr int STAGE_PLAIN = A_BYTES + B_BYTES;          // 24 KB: hiA hiB
-constexpr int STAGES_SPLIT = 4;
-constexpr int STAGES_PLAIN = 8;
+constexpr int STAGE_SPLIT = 2 * A_BYTES + 2 * B_BYTES;  // 96 KB: hiA loA hiB loB
+constexpr int STAGE_PLAIN = A_BYTES + B_BYTES;          // 48 KB: hiA hiB
+constexpr int STAGES_SPLIT = 2;
+constexpr int STAGES_PLAIN = 4;
 constexpr int THREADS = 192;
 
 template <bool SPLIT>
@@ -172,19 +172,19 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t st = smem_u32(smem + stage * STAGE_BYTES);
 #pragma unroll
           for (int ks = 0; ks < BK / UMMA_K; ++ks) {
-            const uint32_t koff = ks * UMMA_K * 2;  // bytes within the 64-byte row
+            const uint32_t koff = ks * UMMA_K * 2;  // bytes within the 128-byte row
             const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
             if (SPLIT) {
-              const uint64_t dhiA = make_desc_sw64(st + koff);
-              const uint64_t dloA = make_desc_sw64(st + A_BYTES + koff);
-              const uint64_t dhiB = make_desc_sw64(st + 2 * A_BYTES + koff);
-              const uint64_t dloB = make_desc_sw64(st + 2 * A_BYTES + B_BYTES + koff);
+              const uint64_t dhiA = make_desc_sw128(st + koff);
+              const uint64_t dloA = make_desc_sw128(st + A_BYTES + koff);
+              const uint64_t dhiB = make_desc_sw128(st + 2 * A_BYTES + koff);
+              const uint64_t dloB = make_desc_sw128(st + 2 * A_BYTES + B_BYTES + koff);
               mma_f16(tmem_base, dhiA, dhiB, acc);              // ACC0 += hi_I hi_J^T
               mma_f16(tmem_base + BN, dloA, dhiB, acc);         // ACC1 += lo_I hi_J^T
               mma_f16(tmem_base + BN, dhiA, dloB, 1u);          // ACC1 += hi_I lo_J^T
             } else {
-              const uint64_t dhiA = make_desc_sw64(st + koff);
-              const uint64_t dhiB = make_desc_sw64(st + A_BYTES + koff);
+              const uint64_t dhiA = make_desc_sw128(st + koff);
+              const uint64_t dhiB = make_desc_sw128(st + A_BYTES + koff);
               mma_f16(tmem_base, dhiA, dhiB, acc);
             }
           }

@@ -11,10 +11,10 @@
 //
 // CTA = 10 warps, persistent over the upper-tile list (one CTA per SM):
 //   warp 0      TMA producer (one thread): hp, lo', hi of the 128 A rows and
-//               hi, lo' of the 256 B rows per 32-wide K stage (56 KB, 4 stages)
+//               hi, lo' of the 256 B rows per 64-wide K stage (112 KB, 2 stages)
 //   warp 1      TMEM allocation + MMA issuer (one thread)
 //   warps 2..9  epilogue: TMEM lane quarter (warp % 4) x column half
-// Plain FP16 (split = false): hi hi only, 24 KB stages, 8 stages.
+// Plain FP16 (split = false): hi hi only, 48 KB stages, 4 stages.
 // Every mbarrier wait is bounded; see syrk_tc.cu for the time-out path.
 #include <cuda.h>
 #include <cuda_fp16.h>
@@ -29,15 +29,15 @@ namespace tc1 {
 
 using namespace sp2::tc;
 
-constexpr int STAGE_SPLIT = 3 * A_BYTES + 2 * B_BYTES;  // 56 KB: hpA loA hiA hiB loB
-constexpr int STAGE_PLAIN = A_BYTES + B_BYTES;          // 24 KB: hiA hiB
-constexpr int STAGES_SPLIT = 4;
-constexpr int STAGES_PLAIN = 8;
+constexpr int STAGE_SPLIT = 3 * A_BYTES + 2 * B_BYTES;  // 112 KB: hpA loA hiA hiB loB
+constexpr int STAGE_PLAIN = A_BYTES + B_BYTES;          // 48 KB: hiA hiB
+constexpr int STAGES_SPLIT = 2;
+constexpr int STAGES_PLAIN = 4;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;  // two 256-column accumulators
 
-// stage offsets (split): hpA 0, loA 8K, hiA 16K, hiB 24K, loB 40K
+// stage offsets (split): hpA, loA, hiA (A_BYTES each), hiB, loB (B_BYTES each)
 constexpr int OFF_HPA = 0, OFF_LOA = A_BYTES, OFF_HIA = 2 * A_BYTES, OFF_HIB = 3 * A_BYTES,
               OFF_LOB = 3 * A_BYTES + B_BYTES;
 
@@ -175,12 +175,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint32_t koff = ks * UMMA_K * 2;
             const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
             if (SPLIT) {
-              const uint64_t dhiB = make_desc_sw64(st + OFF_HIB + koff);
-              mma_f16(d, make_desc_sw64(st + OFF_HPA + koff), dhiB, acc);               // 2^s hi hi
-              mma_f16(d, make_desc_sw64(st + OFF_LOA + koff), dhiB, 1u);                // lo' hi
-              mma_f16(d, make_desc_sw64(st + OFF_HIA + koff), make_desc_sw64(st + OFF_LOB + koff), 1u);  // hi lo'
+              const uint64_t dhiB = make_desc_sw128(st + OFF_HIB + koff);
+              mma_f16(d, make_desc_sw128(st + OFF_HPA + koff), dhiB, acc);               // 2^s hi hi
+              mma_f16(d, make_desc_sw128(st + OFF_LOA + koff), dhiB, 1u);                // lo' hi
+              mma_f16(d, make_desc_sw128(st + OFF_HIA + koff), make_desc_sw128(st + OFF_LOB + koff), 1u);  // hi lo'
             } else {
-              mma_f16(d, make_desc_sw64(st + koff), make_desc_sw64(st + A_BYTES + koff), acc);
+              mma_f16(d, make_desc_sw128(st + koff), make_desc_sw128(st + A_BYTES + koff), acc);
             }
           }
           mma_commit(&empty[stage]);

@@ -13,7 +13,7 @@ namespace tc {
 
 constexpr int BM = kTcBM;           // 128
 constexpr int BN = kTcBN;           // 256
-constexpr int BK = 32;              // K per stage: 32 FP16 = 64 B rows (64-byte swizzle)
+constexpr int BK = 64;              // K per stage: 64 FP16 = 128 B rows (128-byte swizzle)
 constexpr int UMMA_K = 16;          // K per tcgen05.mma (kind::f16)
 constexpr int A_BYTES = BM * BK * 2;   // 8 KB
 constexpr int B_BYTES = BN * BK * 2;   // 16 KB
@@ -97,19 +97,20 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor (tcgen05): K-major operand, 64-byte
-// swizzle, rows of 64 B, 8-row core groups 512 B apart.
+// Shared-memory matrix descriptor (tcgen05): K-major operand, 128-byte
+// swizzle, rows of 128 B, 8-row core groups 1024 B apart.
 //   bits  0-13 start address >> 4
 //   bits 16-29 leading byte offset >> 4 (not used by swizzled K-major; 1)
-//   bits 32-45 stride byte offset >> 4 (512 B)
+//   bits 32-45 stride byte offset >> 4 (1024 B)
 //   bits 46-47 descriptor version (1 on sm_100-class parts)
-//   bits 61-63 swizzle mode (4 = 64-byte)
-__device__ __forceinline__ uint64_t make_desc_sw64(uint32_t saddr) {
+//   bits 61-63 swizzle mode (2 = 128-byte)
+// A K = 16 step inside the 128-byte row advances the start address by 32 B.
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)1u << 16;
-  d |= (uint64_t)(512u >> 4) << 32;
+  d |= (uint64_t)(1024u >> 4) << 32;
   d |= (uint64_t)1u << 46;
-  d |= (uint64_t)4u << 61;
+  d |= (uint64_t)2u << 61;
   return d;
 }
 
