@@ -897,6 +897,7 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
       A.lo_out = (__half*)lo[cur ^ 1];
       A.hp_out = (__half*)hp[cur ^ 1];
       CK(launch_syrk_tc1(A, m[cur], split, grid, st));
+      CK(cudaEventRecord(g.lsq[k], st));
       CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
                         (double2*)part, (unsigned*)tick, rgrid, st));
       CK(cudaEventRecord(g.lev[k + 1], st));
@@ -916,6 +917,7 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
       A.Yin = (float*)Y[cur];
       A.Yout = (float*)Y[cur ^ 1];
       CK(launch_syrk_simt(A, std::min(nt, 65535), st));
+      CK(cudaEventRecord(g.lsq[k], st));
       CK(launch_rownorm((float*)Y[cur ^ 1], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
                         (double2*)part, (unsigned*)tick, rgrid, st));
       CK(cudaEventRecord(g.lev[k + 1], st));
@@ -933,10 +935,21 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   CK(cudaEventElapsedTime(&ms, g.ev0, g.ev1));
   const Ctl* cs = (const Ctl*)hb;
   const int e = *(const int*)((char*)hb + (size_t)B * sizeof(Ctl));
+  float pro = 0.f, lms[SP2_MAX_LAYERS], sms[SP2_MAX_LAYERS];
+  CK(cudaEventElapsedTime(&pro, g.ev0, g.lev[0]));
+  for (int k = 0; k < max_iter + 2; ++k) {
+    CK(cudaEventElapsedTime(&lms[k], g.lev[k], g.lev[k + 1]));
+    CK(cudaEventElapsedTime(&sms[k], g.lev[k], g.lsq[k]));
+  }
   sp2_status worst = SP2_OK;
   for (int b = 0; b < B; ++b) {
     fill_stats(cs[b], &stats[b], ms, prec);
     stats[b].launches = max_iter + 2;
+    stats[b].prologue_ms = pro;
+    for (int k = 0; k < max_iter + 2; ++k) {
+      stats[b].layer_ms[k] = lms[k];
+      stats[b].square_ms[k] = sms[k];
+    }
     const sp2_status sb = status_of(cs[b], e);
     if (sb < 0 && worst >= 0) worst = sb;
     if (sb == SP2_NOT_CONVERGED && worst == SP2_OK) worst = SP2_NOT_CONVERGED;
