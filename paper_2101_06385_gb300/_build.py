@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsp2.so")
 SOURCES = ["api.cu", "prep.cu", "syrk_simt.cu", "syrk_tc.cu", "syrk_tc1.cu", "syrk_tc2.cu", "noalloc.cu"]
-HEADERS = ["common.cuh", "kernels.h", "tile_finish.cuh", "tc_ptx.cuh"]
+HEADERS = ["common.cuh", "kernels.h", "tile_finish.cuh", "tc_ptx.cuh", "epilogue.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                 "-Xcompiler", "-Wno-deprecated-declarations"]

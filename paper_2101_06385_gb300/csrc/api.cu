@@ -795,8 +795,11 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   CKS(ws(B_HS, B * sizeof(float*), &hs));
   CKS(ws(B_DPTR, B * sizeof(float*), &dptr));
   CKS(ws(B_ERR, sizeof(int), &err, true));
-  const int igrid = (int)std::min<long long>(Nmax, std::max(1, 8 * g.num_sms / B + 1));
-  const int rgrid = (int)std::min<long long>((Nmax + 7) / 8, std::max(1, 2 * g.num_sms / B + 1));
+  // per-instance grids: at most 16 rows per block for the input layer and 8
+  // rows per warp for the row norms and bounds
+  const int igrid = (int)std::min<long long>(Nmax, std::max((Nmax + 15) / 16, 8 * g.num_sms / B + 1));
+  const int rgrid = (int)std::min<long long>((Nmax + 7) / 8, std::max((Nmax + 63) / 64, 2 * g.num_sms / B + 1));
+  const int ggrid = rgrid;
   CKS(ws(B_PART, (size_t)B * std::max(igrid, rgrid) * sizeof(double2), &part));
   CKS(ws(B_TICKET, std::max(64, B) * sizeof(unsigned), &tick, true));
   CKS(ws(B_RN, (size_t)B * Nmax * sizeof(double), &rn));
@@ -850,7 +853,8 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   A.err = (int*)err;
 
   CK(cudaEventRecord(g.ev0, st));
-  CK(launch_gershgorin_batched((const float* const*)hs, (const int*)ns, (Ctl*)ctl, B, st));
+  CK(launch_gershgorin_batched((const float* const*)hs, (const int*)ns, (Ctl*)ctl, B, (double2*)part, (unsigned*)tick,
+                               ggrid, st));
   // iterate Y in uniform slots [B][Nmax][ld_y]; D_out[b] is written by the last layer
   const long long ld_y = round_up(Nmax, 4), slot_y = ld_y * Nmax;
   void* Y[2] = {nullptr, nullptr};
@@ -991,7 +995,12 @@ sp2_status network_prologue(const float* H, int B, int N, int L, const float* co
   CK(cudaMemcpyAsync(hs, hh, B * sizeof(void*), cudaMemcpyHostToDevice, g.stream));
   CK(cudaMemcpyAsync(dptr, hd, B * sizeof(void*), cudaMemcpyHostToDevice, g.stream));
   CK(cudaEventRecord(g.stage_done, g.stream));
-  CK(launch_gershgorin_batched((const float* const*)hs, (const int*)ns, (Ctl*)ctl, B, g.stream));
+  const int ggrid = (int)std::min<long long>((N + 7) / 8, std::max((N + 63) / 64, 2 * g.num_sms / B + 1));
+  void *part, *tick;
+  CKS(ws(B_PART, (size_t)B * ggrid * sizeof(double2), &part));
+  CKS(ws(B_TICKET, std::max(64, B) * sizeof(unsigned), &tick, true));
+  CK(launch_gershgorin_batched((const float* const*)hs, (const int*)ns, (Ctl*)ctl, B, (double2*)part, (unsigned*)tick,
+                               ggrid, g.stream));
   // bounds to the host: the FP64 shift sequence is planned there
   void* hb;
   CKS(staging((size_t)B * 2 * sizeof(double) + (size_t)B * sizeof(int), &hb));

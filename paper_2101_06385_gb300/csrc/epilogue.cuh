@@ -1,0 +1,264 @@
+// Epilogue of the single-accumulator tcgen05 squaring kernels (syrk_tc1.cu,
+// syrk_tc2.cu).  Eight warps drain one 128 x 256 FP32 accumulator of
+// 2^s P = 2^s Y^2 (Eq. 14) from TMEM and apply the layer of Alg. 1,
+//     Y' = ca Y + cb P + cc I        (S = alpha I + Y, Eq. 16 form)
+// with the diagonal in FP64 from the row norms (Y^2)_ii = sum_k Y_ik^2,
+// re-split Y' into the FP16 operands of the next layer (Eq. 12), store the
+// upper tile and its mirror, and publish the tile's FP64 (tr Y', ||Y'||_F^2)
+// partial.
+//
+// Warp ew (0..7) owns TMEM lane quarter q (the warp's index mod 4, a
+// hardware rule) and column half ew / 4: 32 rows x 128 columns, drained in
+// four 32-column chunks (tcgen05.ld 32x32b: one row per lane).
+//
+// No named barrier is used: the eight per-warp partials of a tile meet in
+// shared memory and the last warp to arrive (shared atomic counter) sums
+// them in warp order, so the result does not depend on arrival order.  A
+// partial slot is reused four tiles later; a warp can only reach that tile
+// after every warp has released the accumulator two tiles after this one,
+// which each warp does after it has finished this tile, so three slots would
+// do.  A warp whose accumulator wait fails (time-out or abort) leaves
+// without touching the barrier state of the others.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_ptx.cuh"
+#include "tile_finish.cuh"
+
+namespace sp2 {
+namespace epi {
+
+constexpr int WARPS = 8;
+constexpr int SLOTS = 4;
+
+struct Shared {
+  double red[SLOTS][WARPS][2];
+  int cnt[SLOTS];
+};
+
+// thread 0, before the kernel's first __syncthreads
+__device__ __forceinline__ void init(Shared& s) {
+  for (int k = 0; k < SLOTS; ++k) s.cnt[k] = 0;
+}
+
+__device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+// Tile t with accumulator use `it` (buffer it & 1).  Returns 0 when the
+// tile's instance is inactive (nothing issued for it), 1 when done, -1 when
+// the accumulator wait failed.
+template <bool SPLIT>
+__device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_t tmem_base, uint64_t* tmem_full,
+                                    uint64_t* tmem_empty, volatile int* abort_flag, Shared& sh, int ew, int q,
+                                    int lane) {
+  using namespace sp2::tc;
+  int b, I, J, h;
+  unpack_tile(a.tiles[t], b, I, J, h);
+  const LayerParams p = load_params(a, b);
+  if (!p.active) return 0;
+  const int N = a.Ns[b];
+  const int hc = ew >> 2;
+  const int r = I * BN + h * BM + q * 32 + lane;
+  const bool mirror = (I != J);
+  const bool outD = (p.out_mode == OUT_D);
+  const float unscale = SPLIT ? a.lo_unscale : 1.f;
+  const float lo_scale = a.lo_scale;
+  float* Y = a.Yout + (long long)b * a.slot_y;
+  const float* Yold = a.Yin + (long long)b * a.slot_y;
+  const long long ld = a.ld_y;
+
+  // issued before the accumulator wait: the diagonal's FP64 row norm and
+  // the old row segment (into L2)
+  double rn_r = 0.0;
+  if (r < N) {
+    if (!mirror && a.rn) rn_r = a.rn[(long long)b * a.ld_rn + r];
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+      const int c0 = J * BN + hc * 128 + ch * 32;
+      if (c0 < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(Yold + (long long)r * ld + c0));
+    }
+  }
+
+  const uint32_t buf = it & 1u;
+  const bool got = __all_sync(0xffffffffu, mbar_wait(&tmem_full[buf], (it >> 1) & 1u, abort_flag));
+  if (!got) {
+    if (lane == 0) atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
+    *abort_flag = 1;
+    return -1;
+  }
+  tc_fence_after();
+
+  __half* ho = a.hi_out ? a.hi_out + (long long)b * a.slot_h : nullptr;
+  __half* lo_ = a.lo_out ? a.lo_out + (long long)b * a.slot_h : nullptr;
+  __half* hp_ = a.hp_out ? a.hp_out + (long long)b * a.slot_h : nullptr;
+  const long long ldh = a.ld_h;
+  float* D = outD ? a.Dptr[b] : nullptr;
+  double tr = 0.0, sq = 0.0;
+  const uint32_t taddr = tmem_base + buf * BN + ((uint32_t)(q * 32) << 16) + hc * 128;
+  const bool vec_y = (ld & 3) == 0;
+
+#pragma unroll 1
+  for (int ch = 0; ch < 4; ++ch) {
+    uint32_t v[32];
+    __syncwarp();
+    tmem_ld32(taddr + ch * 32, v);
+    tmem_ld_wait();
+    if (ch == 3) {
+      // accumulator drained: the MMA issuer may reuse this buffer
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tmem_empty[buf]);
+    }
+    const int c0 = J * BN + hc * 128 + ch * 32;
+    // the diagonal element of row r, if it lies in this chunk (I == J only)
+    const int jd = r - c0;
+    const bool dchunk = !mirror && (unsigned)jd < 32u;
+    float y[32];
+    if (r < N) {
+      const bool full_chunk = (c0 + 32 <= N) && vec_y;
+      if (full_chunk) {
+        const float4* src = reinterpret_cast<const float4*>(Yold + (long long)r * ld + c0);
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+          const float4 o = src[j4];
+          y[4 * j4 + 0] = o.x;
+          y[4 * j4 + 1] = o.y;
+          y[4 * j4 + 2] = o.z;
+          y[4 * j4 + 3] = o.w;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) y[j] = (c0 + j < N) ? Yold[(long long)r * ld + c0 + j] : 0.f;
+      }
+      float yold_d = 0.f, p_d = 0.f;
+      if (dchunk) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j == jd) {
+            yold_d = y[j];
+            p_d = __uint_as_float(v[j]) * unscale;
+          }
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float P = __uint_as_float(v[j]) * unscale;
+        const float yn = fmaf(p.ca, y[j], p.cb * P);
+        y[j] = (c0 + j < N) ? yn : 0.f;
+      }
+      // one FP64 update per row, outside the unrolled element loop
+      float ydo = 0.f;
+      if (dchunk) {
+        const double pd = a.rn ? rn_r : (double)p_d;
+        const double yd = p.ca_d * (double)yold_d + p.cb_d * pd + p.cc_d;
+        tr += yd;
+        const float ydf = (float)yd;
+        ydo = outD ? (float)(yd + p.alpha_out) : ydf;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j == jd) y[j] = ydf;
+      }
+      float sqf = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) sqf = fmaf(y[j], y[j], sqf);
+      sq += (double)sqf;
+      if (outD) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < N) D[(long long)r * N + c0 + j] = (dchunk && j == jd) ? ydo : y[j];
+      } else {
+        if (full_chunk) {
+          float4* dst = reinterpret_cast<float4*>(Y + (long long)r * ld + c0);
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4) dst[j4] = make_float4(y[4 * j4], y[4 * j4 + 1], y[4 * j4 + 2], y[4 * j4 + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (c0 + j < N) Y[(long long)r * ld + c0 + j] = y[j];
+        }
+        if (ho && c0 + 32 <= (int)ldh) {
+          // 32 halves per part, packed in registers; columns >= N carry zeros
+          uint32_t ph[16], pl[16], pp[16];
+#pragma unroll
+          for (int j2 = 0; j2 < 16; ++j2) {
+            __half h0, l0, h1, l1;
+            split_fp16(y[2 * j2], lo_scale, h0, l0);
+            split_fp16(y[2 * j2 + 1], lo_scale, h1, l1);
+            ph[j2] = pack_h2(h0, h1);
+            pl[j2] = pack_h2(l0, l1);
+            pp[j2] = pack_h2(__float2half_rn(__half2float(h0) * lo_scale), __float2half_rn(__half2float(h1) * lo_scale));
+          }
+          uint4* dh = reinterpret_cast<uint4*>(ho + (long long)r * ldh + c0);
+#pragma unroll
+          for (int j4 = 0; j4 < 4; ++j4) dh[j4] = make_uint4(ph[4 * j4], ph[4 * j4 + 1], ph[4 * j4 + 2], ph[4 * j4 + 3]);
+          if (lo_) {
+            uint4* dl = reinterpret_cast<uint4*>(lo_ + (long long)r * ldh + c0);
+#pragma unroll
+            for (int j4 = 0; j4 < 4; ++j4)
+              dl[j4] = make_uint4(pl[4 * j4], pl[4 * j4 + 1], pl[4 * j4 + 2], pl[4 * j4 + 3]);
+          }
+          if (hp_) {
+            uint4* dp = reinterpret_cast<uint4*>(hp_ + (long long)r * ldh + c0);
+#pragma unroll
+            for (int j4 = 0; j4 < 4; ++j4)
+              dp[j4] = make_uint4(pp[4 * j4], pp[4 * j4 + 1], pp[4 * j4 + 2], pp[4 * j4 + 3]);
+          }
+        }
+      }
+    }
+    // mirrored store: lanes hold consecutive rows r -> consecutive columns
+    if (mirror && r < N) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = c0 + j;
+        if (c < N) {
+          if (outD) {
+            D[(long long)c * N + r] = y[j];
+          } else {
+            Y[(long long)c * ld + r] = y[j];
+            if (ho) {
+              __half hh, ll;
+              split_fp16(y[j], lo_scale, hh, ll);
+              ho[(long long)c * ldh + r] = hh;
+              if (lo_) lo_[(long long)c * ldh + r] = ll;
+              if (hp_) hp_[(long long)c * ldh + r] = __float2half_rn(__half2float(hh) * lo_scale);
+            }
+          }
+        }
+      }
+    }
+  }
+
+  if (mirror) sq *= 2.0;
+  tr = warp_sum_d(tr);
+  sq = warp_sum_d(sq);
+  const int slot = (int)(it & (SLOTS - 1));
+  unsigned last = 0;
+  if (lane == 0) {
+    sh.red[slot][ew][0] = tr;
+    sh.red[slot][ew][1] = sq;
+    __threadfence_block();
+    last = (atomicAdd(&sh.cnt[slot], 1) == WARPS - 1) ? 1u : 0u;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last) {
+    __threadfence_block();
+    double T = 0.0, Q = 0.0;
+    if (lane == 0) {
+      volatile double* rd = &sh.red[slot][0][0];
+      for (int k = 0; k < WARPS; ++k) {
+        T += rd[2 * k];
+        Q += rd[2 * k + 1];
+      }
+      sh.cnt[slot] = 0;
+    }
+    finish_tile_warp(a, t, b, T, Q, p.out_mode);
+  }
+  return 1;
+}
+
+}  // namespace epi
+}  // namespace sp2

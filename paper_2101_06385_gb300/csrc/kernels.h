@@ -57,7 +57,8 @@ constexpr int kSimtB = 128;  // FFMA tile
 
 cudaError_t launch_gershgorin(const float* H, int N, long long ld, long long slot, int B, double2* partials,
                               unsigned* ticket, Ctl* ctl, double* bounds_out, int grid, cudaStream_t st);
-cudaError_t launch_gershgorin_batched(const float* const* Hs, const int* Ns, Ctl* ctl, int batch, cudaStream_t st);
+cudaError_t launch_gershgorin_batched(const float* const* Hs, const int* Ns, Ctl* ctl, int batch, double2* partials,
+                                     unsigned* tickets, int grid_x, cudaStream_t st);
 cudaError_t launch_input_layer(const float* const* Hs, const int* Ns, long long ld_in, float* Y, long long ld_y,
                                long long slot_y, __half* hi, __half* lo, __half* hp, long long ld_h, long long slot_h,
                                int rows_pad, int cols_pad, float lo_scale, Ctl* ctl, const double* bounds, double2* partials, unsigned* tickets,

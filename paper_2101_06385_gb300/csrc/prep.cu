@@ -111,20 +111,40 @@ __global__ void __launch_bounds__(256) gershgorin_kernel(const float* __restrict
   }
 }
 
-// Per-instance Gershgorin for the batched path: one block per instance
-// (instances are small), results into ctl[b].
+// Per-instance Gershgorin for the batched path: grid (blocks, instances),
+// one warp per row as above, per-block partials, and the last block of each
+// instance folds them into ctl[b].
 __global__ void __launch_bounds__(256) gershgorin_batched_kernel(const float* const* __restrict__ Hs,
-                                                                 const int* __restrict__ Ns, Ctl* __restrict__ ctl) {
-  const int b = blockIdx.x;
+                                                                 const int* __restrict__ Ns, Ctl* __restrict__ ctl,
+                                                                 double2* __restrict__ partials,
+                                                                 unsigned* __restrict__ tickets) {
+  const int b = blockIdx.y;
   const int N = Ns[b];
   const float* H = Hs[b];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool vec = ((N & 3) == 0) && ((((uintptr_t)H) & 15) == 0);
   double lo = INFINITY, hi = -INFINITY;
   bool bad = false;
-  for (int i = warp; i < N; i += 8) {
+  for (int i = blockIdx.x * 8 + warp; i < N; i += gridDim.x * 8) {
     const float* row = H + (long long)i * N;
     double acc = 0.0;
-    for (int j = lane; j < N; j += 32) acc += (double)fabsf(row[j]);
+    if (vec) {
+      const float4* r4 = reinterpret_cast<const float4*>(row);
+      const int n4 = N >> 2;
+      for (int j0 = 0; j0 < n4; j0 += 4 * 32) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u * 32 + lane;
+          v[u] = (j < n4) ? __ldcs(r4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          acc += (double)((fabsf(v[u].x) + fabsf(v[u].y)) + (fabsf(v[u].z) + fabsf(v[u].w)));
+      }
+    } else {
+      for (int j = lane; j < N; j += 32) acc += (double)fabsf(row[j]);
+    }
     acc = warp_sum_d(acc);
     const double d = (double)row[i];
     const double R = acc - fabs(d);
@@ -142,13 +162,30 @@ __global__ void __launch_bounds__(256) gershgorin_batched_kernel(const float* co
     if (bad) atomicOr(&s_bad, 1);
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double L = INFINITY, U = -INFINITY;
-  bool nan_seen = s_bad != 0;
-  for (int w = 0; w < 8; ++w) {
-    L = fmin(L, s_lo[w]);
-    U = fmax(U, s_hi[w]);
+  __shared__ bool s_last;
+  double2* part = partials + (long long)b * gridDim.x;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < 8; ++w) {
+      lo = fmin(lo, s_lo[w]);
+      hi = fmax(hi, s_hi[w]);
+    }
+    if (s_bad) lo = hi = NAN;
+    part[blockIdx.x] = make_double2(lo, hi);
+    __threadfence();
+    s_last = (atomicAdd(&tickets[b], 1u) == gridDim.x - 1);
   }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double L = INFINITY, U = -INFINITY;
+  bool nan_seen = false;
+  for (unsigned k = 0; k < gridDim.x; ++k) {
+    const double2 p = __ldcg(&part[k]);
+    if (isnan(p.x) || isnan(p.y)) nan_seen = true;
+    L = fmin(L, p.x);
+    U = fmax(U, p.y);
+  }
+  tickets[b] = 0u;
   Ctl* c = ctl + b;
   c->e_min = L;
   c->e_max = U;
@@ -439,8 +476,10 @@ cudaError_t launch_gershgorin(const float* H, int N, long long ld, long long slo
   return cudaGetLastError();
 }
 
-cudaError_t launch_gershgorin_batched(const float* const* Hs, const int* Ns, Ctl* ctl, int batch, cudaStream_t st) {
-  gershgorin_batched_kernel<<<batch, 256, 0, st>>>(Hs, Ns, ctl);
+cudaError_t launch_gershgorin_batched(const float* const* Hs, const int* Ns, Ctl* ctl, int batch, double2* partials,
+                                     unsigned* tickets, int grid_x, cudaStream_t st) {
+  dim3 grid(grid_x, batch);
+  gershgorin_batched_kernel<<<grid, 256, 0, st>>>(Hs, Ns, ctl, partials, tickets);
   return cudaGetLastError();
 }
 

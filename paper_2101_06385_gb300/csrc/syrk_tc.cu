@@ -222,6 +222,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int cb0 = J * BN;
       const bool mirror = (I != J);
       const bool outD = (p.out_mode == OUT_D);
+      // FP64 row norm for the diagonal, fetched before the accumulator wait
+      const double rn_r = (!mirror && a.rn && r < N) ? a.rn[(long long)b * a.ld_rn + r] : 0.0;
       const bool got = mbar_wait(tmem_full, acc_phase, abort_flag);
       // the four epilogue warps take one decision: go on only if all of them
       // saw the accumulator arrive (s_got is rewritten only after the
@@ -272,6 +274,18 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int j = 0; j < 32; ++j) y[j] = (c0 + j < N) ? Yold[(long long)r * ld + c0 + j] : 0.f;
           }
+          // the diagonal element of row r, if it lies in this chunk (I == J only)
+          const int jd = r - c0;
+          const bool dchunk = !mirror && (unsigned)jd < 32u;
+          float yold_d = 0.f, p_d = 0.f;
+          if (dchunk) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j == jd) {
+                yold_d = y[j];
+                p_d = SPLIT ? fmaf(__uint_as_float(v1[j]), a.lo_unscale, __uint_as_float(v0[j])) : __uint_as_float(v0[j]);
+              }
+          }
           if (a.aux) {
             // adjoint mode: tr Yin, <Yin, aux>, <P, aux> on the old values
             const float* ax = a.aux + (long long)b * a.slot_y + (long long)r * ld + c0;
@@ -283,30 +297,32 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const float P = SPLIT ? fmaf(__uint_as_float(v1[j]), a.lo_unscale, __uint_as_float(v0[j])) : __uint_as_float(v0[j]);
                 gy = fmaf(y[j], xv, gy);
                 py = fmaf(P, xv, py);
-                if (r == c0 + j) dtr += (double)y[j];
               }
             }
+            if (dchunk) dtr += (double)yold_d;
             dgy += (double)gy;
             dpy += (double)py;
           }
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const float P = SPLIT ? fmaf(__uint_as_float(v1[j]), a.lo_unscale, __uint_as_float(v0[j])) : __uint_as_float(v0[j]);
-            float yn;
-            if (r == c0 + j) {
-              // diagonal of Y^2 from the FP64 row norms (unbiased), update in FP64
-              const double pd = a.rn ? a.rn[(long long)b * a.ld_rn + r] : (double)P;
-              const double yd = p.ca_d * (double)y[j] + p.cb_d * pd + p.cc_d;
-              tr += yd;
-              yn = (float)yd;
-              if (outD) ydiag = (float)(yd + p.alpha_out);
-            } else {
-              yn = fmaf(p.ca, y[j], p.cb * P);
-            }
-            if (c0 + j >= N) yn = 0.f;
-            y[j] = yn;
-            sqf = fmaf(yn, yn, sqf);
+            const float yn = fmaf(p.ca, y[j], p.cb * P);
+            y[j] = (c0 + j < N) ? yn : 0.f;
           }
+          if (dchunk) {
+            // diagonal of Y^2 from the FP64 row norms (unbiased), update in
+            // FP64, once per row outside the unrolled element loop
+            const double pd = a.rn ? rn_r : (double)p_d;
+            const double yd = p.ca_d * (double)yold_d + p.cb_d * pd + p.cc_d;
+            tr += yd;
+            const float ydf = (float)yd;
+            if (outD) ydiag = (float)(yd + p.alpha_out);
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j == jd) y[j] = ydf;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) sqf = fmaf(y[j], y[j], sqf);
           sq += (double)sqf;
           if (outD) {
 #pragma unroll

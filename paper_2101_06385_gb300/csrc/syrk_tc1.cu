@@ -22,7 +22,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "tc_ptx.cuh"
-#include "tile_finish.cuh"
+#include "epilogue.cuh"
 
 namespace sp2 {
 namespace tc1 {
@@ -33,17 +33,13 @@ constexpr int STAGE_SPLIT = 3 * A_BYTES + 2 * B_BYTES;  // 112 KB: hpA loA hiA h
 constexpr int STAGE_PLAIN = A_BYTES + B_BYTES;          // 48 KB: hiA hiB
 constexpr int STAGES_SPLIT = 2;
 constexpr int STAGES_PLAIN = 4;
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = epi::WARPS;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;  // two 256-column accumulators
 
 // stage offsets (split): hpA, loA, hiA (A_BYTES each), hiB, loB (B_BYTES each)
 constexpr int OFF_HPA = 0, OFF_LOA = A_BYTES, OFF_HIA = 2 * A_BYTES, OFF_HIB = 3 * A_BYTES,
               OFF_LOB = 3 * A_BYTES + B_BYTES;
-
-__device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
-  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
-}
 
 template <bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -62,14 +58,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* drain = tmem_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   __shared__ int s_abort;
-  __shared__ double s_red[EPI_WARPS][2];
-  __shared__ int s_got[EPI_WARPS];
+  __shared__ epi::Shared s_epi;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     s_abort = 0;
+    epi::init(s_epi);
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
@@ -204,186 +200,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int ew = warp - 2;                 // 0..7
-    const int q = warp & 3;                  // TMEM lane quarter
-    const int hc = ew >> 2;                  // column half of the 256-wide tile
-    const int row_local = q * 32 + lane;
-    const float unscale = SPLIT ? a.lo_unscale : 1.f;
-    const float lo_scale = a.lo_scale;
+    const int ew = warp - 2;  // 0..7
+    const int q = warp & 3;   // TMEM lane quarter
     uint32_t it = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-      int b, I, J, h;
-      unpack_tile(a.tiles[t], b, I, J, h);
-      const LayerParams p = load_params(a, b);
-      if (!p.active) continue;
-      const int N = a.Ns[b];
-      const int r = I * BN + h * BM + row_local;
-      const bool mirror = (I != J);
-      const bool outD = (p.out_mode == OUT_D);
-      const uint32_t buf = it & 1u;
-      const bool got = mbar_wait(&tmem_full[buf], (it >> 1) & 1u, abort_flag);
-      if (lane == 0) s_got[ew] = got ? 1 : 0;
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      int all = 1;
-#pragma unroll
-      for (int k = 0; k < EPI_WARPS; ++k) all &= s_got[k];
-      if (!all) {
-        if (!got && lane == 0) atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
-        break;
-      }
-      tc_fence_after();
-
-      float* Y = a.Yout + (long long)b * a.slot_y;
-      const float* Yold = a.Yin + (long long)b * a.slot_y;
-      const long long ld = a.ld_y;
-      __half* ho = a.hi_out ? a.hi_out + (long long)b * a.slot_h : nullptr;
-      __half* lo_ = a.lo_out ? a.lo_out + (long long)b * a.slot_h : nullptr;
-      __half* hp_ = a.hp_out ? a.hp_out + (long long)b * a.slot_h : nullptr;
-      const long long ldh = a.ld_h;
-      float* D = outD ? a.Dptr[b] : nullptr;
-      double tr = 0.0, sq = 0.0;
-      const uint32_t taddr = tmem_base + buf * BN + ((uint32_t)(q * 32) << 16) + hc * 128;
-      const bool vec_y = (ld & 3) == 0;
-
-#pragma unroll 1
-      for (int ch = 0; ch < 4; ++ch) {
-        uint32_t v[32];
-        __syncwarp();
-        tmem_ld32(taddr + ch * 32, v);
-        tmem_ld_wait();
-        if (ch == 3) {
-          // accumulator drained: the MMA issuer may reuse this buffer
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&tmem_empty[buf]);
-        }
-        const int c0 = J * BN + hc * 128 + ch * 32;
-        float y[32];
-        float ydiag = 0.f;
-        if (r < N) {
-          const bool full_chunk = (c0 + 32 <= N) && vec_y;
-          if (full_chunk) {
-            const float4* src = reinterpret_cast<const float4*>(Yold + (long long)r * ld + c0);
-#pragma unroll
-            for (int j4 = 0; j4 < 8; ++j4) {
-              const float4 o = src[j4];
-              y[4 * j4 + 0] = o.x;
-              y[4 * j4 + 1] = o.y;
-              y[4 * j4 + 2] = o.z;
-              y[4 * j4 + 3] = o.w;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) y[j] = (c0 + j < N) ? Yold[(long long)r * ld + c0 + j] : 0.f;
-          }
-          float sqf = 0.f;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float P = __uint_as_float(v[j]) * unscale;
-            float yn;
-            if (r == c0 + j) {
-              const double pd = a.rn ? a.rn[(long long)b * a.ld_rn + r] : (double)P;
-              const double yd = p.ca_d * (double)y[j] + p.cb_d * pd + p.cc_d;
-              tr += yd;
-              yn = (float)yd;
-              if (outD) ydiag = (float)(yd + p.alpha_out);
-            } else {
-              yn = fmaf(p.ca, y[j], p.cb * P);
-            }
-            if (c0 + j >= N) yn = 0.f;
-            y[j] = yn;
-            sqf = fmaf(yn, yn, sqf);
-          }
-          sq += (double)sqf;
-          if (outD) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (c0 + j < N) D[(long long)r * N + c0 + j] = (r == c0 + j) ? ydiag : y[j];
-          } else {
-            if (full_chunk) {
-              float4* dst = reinterpret_cast<float4*>(Y + (long long)r * ld + c0);
-#pragma unroll
-              for (int j4 = 0; j4 < 8; ++j4)
-                dst[j4] = make_float4(y[4 * j4], y[4 * j4 + 1], y[4 * j4 + 2], y[4 * j4 + 3]);
-            } else {
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (c0 + j < N) Y[(long long)r * ld + c0 + j] = y[j];
-            }
-            if (ho && c0 + 32 <= (int)ldh) {
-              // 32 halves per part, packed in registers; columns >= N carry zeros
-              uint32_t ph[16], pl[16], pp[16];
-#pragma unroll
-              for (int j2 = 0; j2 < 16; ++j2) {
-                __half h0, l0, h1, l1;
-                split_fp16(y[2 * j2], lo_scale, h0, l0);
-                split_fp16(y[2 * j2 + 1], lo_scale, h1, l1);
-                ph[j2] = pack_h2(h0, h1);
-                pl[j2] = pack_h2(l0, l1);
-                pp[j2] = pack_h2(__float2half_rn(__half2float(h0) * lo_scale),
-                                 __float2half_rn(__half2float(h1) * lo_scale));
-              }
-              uint4* dh = reinterpret_cast<uint4*>(ho + (long long)r * ldh + c0);
-#pragma unroll
-              for (int j4 = 0; j4 < 4; ++j4)
-                dh[j4] = make_uint4(ph[4 * j4], ph[4 * j4 + 1], ph[4 * j4 + 2], ph[4 * j4 + 3]);
-              if (lo_) {
-                uint4* dl = reinterpret_cast<uint4*>(lo_ + (long long)r * ldh + c0);
-#pragma unroll
-                for (int j4 = 0; j4 < 4; ++j4)
-                  dl[j4] = make_uint4(pl[4 * j4], pl[4 * j4 + 1], pl[4 * j4 + 2], pl[4 * j4 + 3]);
-              }
-              if (hp_) {
-                uint4* dp = reinterpret_cast<uint4*>(hp_ + (long long)r * ldh + c0);
-#pragma unroll
-                for (int j4 = 0; j4 < 4; ++j4)
-                  dp[j4] = make_uint4(pp[4 * j4], pp[4 * j4 + 1], pp[4 * j4 + 2], pp[4 * j4 + 3]);
-              }
-            }
-          }
-        }
-        // mirrored store: lanes hold consecutive rows r -> consecutive columns
-        if (mirror && r < N) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int c = c0 + j;
-            if (c < N) {
-              if (outD) {
-                D[(long long)c * N + r] = y[j];
-              } else {
-                Y[(long long)c * ld + r] = y[j];
-                if (ho) {
-                  __half hh, ll;
-                  split_fp16(y[j], lo_scale, hh, ll);
-                  ho[(long long)c * ldh + r] = hh;
-                  if (lo_) lo_[(long long)c * ldh + r] = ll;
-                  if (hp_) hp_[(long long)c * ldh + r] = __float2half_rn(__half2float(hh) * lo_scale);
-                }
-              }
-            }
-          }
-        }
-      }
-
-      if (mirror) sq *= 2.0;
-      tr = warp_sum_d(tr);
-      sq = warp_sum_d(sq);
-      if (lane == 0) {
-        s_red[ew][0] = tr;
-        s_red[ew][1] = sq;
-      }
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (ew == 0) {
-        double T = 0.0, Q = 0.0;
-        if (lane == 0)
-          for (int k = 0; k < EPI_WARPS; ++k) {
-            T += s_red[k][0];
-            Q += s_red[k][1];
-          }
-        finish_tile_warp(a, t, b, T, Q, p.out_mode);
-      }
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      ++it;
+      const int rc = epi::tile<SPLIT>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag, s_epi, ew, q, lane);
+      if (rc < 0) break;
+      it += (uint32_t)rc;
     }
   }
 
