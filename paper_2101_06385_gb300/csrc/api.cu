@@ -240,20 +240,32 @@ sp2_status tmaps_for(const void* hi, const void* lo, int N, int B, long long ld_
   return SP2_OK;
 }
 
-// Tensor maps {hp(A box), lo(A box), hi(A box), hi(B box), lo(B box)} for the
-// single-accumulator squaring kernel (hp, lo may be null for plain FP16).
-sp2_status tmaps5_for(const void* hp, const void* lo, const void* hi, int N, int B, long long ld_h, long long slot_h,
-                      CUtensorMap* m, int box_b = kTcBN) {
-  const void* hp_ = hp ? hp : hi;
-  const void* lo_ = lo ? lo : hi;
-  bool ok = make_tmap_f16(&m[0], hp_, N, N, B, ld_h, slot_h, 64, kTcBM) &&
-            make_tmap_f16(&m[1], lo_, N, N, B, ld_h, slot_h, 64, kTcBM) &&
-            make_tmap_f16(&m[2], hi, N, N, B, ld_h, slot_h, 64, kTcBM) &&
-            make_tmap_f16(&m[3], hi, N, N, B, ld_h, slot_h, 64, box_b) &&
-            make_tmap_f16(&m[4], lo_, N, N, B, ld_h, slot_h, 64, box_b);
+// Tensor maps {p0(A box), p1(A box), p0(B box), p1(B box)} for the
+// single-accumulator squaring kernels: p0 = hp = 2^s hi and p1 = lo' for the
+// split product, p0 = hi (p1 unused, null) for plain FP16.
+sp2_status tmaps4_for(const void* p0, const void* p1, int N, int B, long long ld_h, long long slot_h, CUtensorMap* m,
+                      int box_b = kTcBN) {
+  const void* p1_ = p1 ? p1 : p0;
+  bool ok = make_tmap_f16(&m[0], p0, N, N, B, ld_h, slot_h, 64, kTcBM) &&
+            make_tmap_f16(&m[1], p1_, N, N, B, ld_h, slot_h, 64, kTcBM) &&
+            make_tmap_f16(&m[2], p0, N, N, B, ld_h, slot_h, 64, box_b) &&
+            make_tmap_f16(&m[3], p1_, N, N, B, ld_h, slot_h, 64, box_b);
   if (!ok) {
     set_err("cuTensorMapEncodeTiled failed (N=%d, ld=%lld)", N, ld_h);
     return SP2_ERR_CUDA;
+  }
+  return SP2_OK;
+}
+
+// FP16 operand planes of the single-accumulator kernels in buffer set k
+// (0, 1): hp and lo' (split) or hi (plain); the others stay null.
+sp2_status planes_for(bool split, int k, size_t bytes, void** hi, void** lo, void** hp) {
+  *hi = *lo = *hp = nullptr;
+  if (split) {
+    CKS(ws(k ? B_LO1 : B_LO0, bytes, lo));
+    CKS(ws(k ? B_HP1 : B_HP0, bytes, hp));
+  } else {
+    CKS(ws(k ? B_HI1 : B_HI0, bytes, hi));
   }
   return SP2_OK;
 }
@@ -540,17 +552,13 @@ sp2_status sp2_layer(const float* X, int B, int N, float a, float b, float c, fl
   A.ld_rn = N;
   if (tc) {
     const long long ld_h = round_up(N, 64), slot_h = ld_h * N;
-    void *hi, *lo = nullptr, *hp = nullptr;
-    CKS(ws(B_HI0, (size_t)slot_h * B * 2, &hi));
-    if (split) {
-      CKS(ws(B_LO0, (size_t)slot_h * B * 2, &lo));
-      CKS(ws(B_HP0, (size_t)slot_h * B * 2, &hp));
-    }
+    void *hi, *lo, *hp;
+    CKS(planes_for(split, 0, (size_t)slot_h * B * 2, &hi, &lo, &hp));
     const int grid = (int)std::min<long long>((long long)N * B, 8LL * g.num_sms);
     CK(launch_split_pad(X, N, (long long)N * N, N, B, A.lo_scale, (__half*)hi, (__half*)lo, (__half*)hp, ld_h, slot_h, grid,
                         g.stream));
-    CUtensorMap m[5];
-    CKS(tmaps5_for(hp, lo, hi, N, B, ld_h, slot_h, m));
+    CUtensorMap m[4];
+    CKS(tmaps4_for(split ? hp : hi, lo, N, B, ld_h, slot_h, m));
     A.hi_out = nullptr;
     A.lo_out = nullptr;
     A.hp_out = nullptr;
@@ -647,15 +655,9 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
 
   if (tc) {
     const long long ld_h = round_up(N, 64), slot_h = ld_h * N;
-    void *hi[2], *lo[2] = {nullptr, nullptr}, *hp[2] = {nullptr, nullptr};
-    CKS(ws(B_HI0, (size_t)slot_h * 2, &hi[0]));
-    CKS(ws(B_HI1, (size_t)slot_h * 2, &hi[1]));
-    if (split) {
-      CKS(ws(B_LO0, (size_t)slot_h * 2, &lo[0]));
-      CKS(ws(B_LO1, (size_t)slot_h * 2, &lo[1]));
-      CKS(ws(B_HP0, (size_t)slot_h * 2, &hp[0]));
-      CKS(ws(B_HP1, (size_t)slot_h * 2, &hp[1]));
-    }
+    void *hi[2], *lo[2], *hp[2];
+    CKS(planes_for(split, 0, (size_t)slot_h * 2, &hi[0], &lo[0], &hp[0]));
+    CKS(planes_for(split, 1, (size_t)slot_h * 2, &hi[1], &lo[1], &hp[1]));
     // K2: Y_0 into D_out, split into buffer 0
     // Buffers hold N rows of ld_h columns; the tensor maps declare N x N, so
     // TMA zero-fills every element outside the matrix.
@@ -665,10 +667,10 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
     // FP64 row norms of Y_0 and the first control step (sigma_1, IdErr_1)
     CK(launch_rownorm(D_out, N, (long long)N * N, (const int*)ns, 1, N, (double*)rn, N, (Ctl*)ctl, (double2*)part,
                       (unsigned*)tick, rgrid, st));
-    CUtensorMap m[2][5];
+    CUtensorMap m[2][4];
     const int boxb = g.pair_kernel ? kTcBM : kTcBN;
-    CKS(tmaps5_for(hp[0], lo[0], hi[0], N, 1, ld_h, slot_h, m[0], boxb));
-    CKS(tmaps5_for(hp[1], lo[1], hi[1], N, 1, ld_h, slot_h, m[1], boxb));
+    CKS(tmaps4_for(split ? hp[0] : hi[0], lo[0], N, 1, ld_h, slot_h, m[0], boxb));
+    CKS(tmaps4_for(split ? hp[1] : hi[1], lo[1], N, 1, ld_h, slot_h, m[1], boxb));
     A.Yin = D_out;
     A.Yout = D_out;
     A.ld_y = N;
@@ -861,32 +863,23 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   CKS(ws(B_Y0, (size_t)slot_y * B * 4, &Y[0]));
   if (tc) {
     const long long ld_h = round_up(Nmax, 64), slot_h = ld_h * Nmax;
-    void *hi[2], *lo[2] = {nullptr, nullptr}, *hp[2] = {nullptr, nullptr};
-    CKS(ws(B_HI0, (size_t)slot_h * B * 2, &hi[0]));
-    CKS(ws(B_HI1, (size_t)slot_h * B * 2, &hi[1]));
-    if (split) {
-      CKS(ws(B_LO0, (size_t)slot_h * B * 2, &lo[0]));
-      CKS(ws(B_LO1, (size_t)slot_h * B * 2, &lo[1]));
-      CKS(ws(B_HP0, (size_t)slot_h * B * 2, &hp[0]));
-      CKS(ws(B_HP1, (size_t)slot_h * B * 2, &hp[1]));
-    }
+    void *hi[2], *lo[2], *hp[2];
+    CKS(planes_for(split, 0, (size_t)slot_h * B * 2, &hi[0], &lo[0], &hp[0]));
+    CKS(planes_for(split, 1, (size_t)slot_h * B * 2, &hi[1], &lo[1], &hp[1]));
     // Slots are Nmax x Nmax in the tensor maps: everything outside instance b's
     // N_b x N_b block must read as zero.  The input layer zero-fills buffer 0's
     // slot; the epilogues never write outside N_b x N_b (row tails up to the
     // 32-column chunk are written as zeros), so buffer 1 is cleared here.
-    CK(cudaMemsetAsync(hi[1], 0, (size_t)slot_h * B * 2, st));
-    if (split) {
-      CK(cudaMemsetAsync(lo[1], 0, (size_t)slot_h * B * 2, st));
-      CK(cudaMemsetAsync(hp[1], 0, (size_t)slot_h * B * 2, st));
-    }
+    for (void* pl : {hi[1], lo[1], hp[1]})
+      if (pl) CK(cudaMemsetAsync(pl, 0, (size_t)slot_h * B * 2, st));
     CK(launch_input_layer((const float* const*)hs, (const int*)ns, 0, (float*)Y[0], ld_y, slot_y, (__half*)hi[0],
                           (__half*)lo[0], (__half*)hp[0], ld_h, slot_h, Nmax, (int)ld_h, A.lo_scale, (Ctl*)ctl, nullptr,
                           (double2*)part, (unsigned*)tick, g.shift, 1, B, igrid, st));
     CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
                       (double2*)part, (unsigned*)tick, rgrid, st));
-    CUtensorMap m[2][5];
-    CKS(tmaps5_for(hp[0], lo[0], hi[0], Nmax, B, ld_h, slot_h, m[0]));
-    CKS(tmaps5_for(hp[1], lo[1], hi[1], Nmax, B, ld_h, slot_h, m[1]));
+    CUtensorMap m[2][4];
+    CKS(tmaps4_for(split ? hp[0] : hi[0], lo[0], Nmax, B, ld_h, slot_h, m[0]));
+    CKS(tmaps4_for(split ? hp[1] : hi[1], lo[1], Nmax, B, ld_h, slot_h, m[1]));
     A.Yin = (float*)Y[0];
     A.Yout = (float*)Y[0];
     A.ld_y = ld_y;
@@ -1120,20 +1113,14 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
   void* Y[2] = {X_out, nullptr};
   void *hi[2] = {nullptr, nullptr}, *lo[2] = {nullptr, nullptr}, *hp[2] = {nullptr, nullptr};
   long long ld_h = 0, slot_h = 0;
-  CUtensorMap m[2][5];
+  CUtensorMap m[2][4];
   if (tc) {
     ld_h = round_up(N, 64);
     slot_h = ld_h * N;
-    CKS(ws(B_HI0, (size_t)slot_h * B * 2, &hi[0]));
-    CKS(ws(B_HI1, (size_t)slot_h * B * 2, &hi[1]));
-    if (split) {
-      CKS(ws(B_LO0, (size_t)slot_h * B * 2, &lo[0]));
-      CKS(ws(B_LO1, (size_t)slot_h * B * 2, &lo[1]));
-      CKS(ws(B_HP0, (size_t)slot_h * B * 2, &hp[0]));
-      CKS(ws(B_HP1, (size_t)slot_h * B * 2, &hp[1]));
-    }
-    CKS(tmaps5_for(hp[0], lo[0], hi[0], N, B, ld_h, slot_h, m[0]));
-    CKS(tmaps5_for(hp[1], lo[1], hi[1], N, B, ld_h, slot_h, m[1]));
+    CKS(planes_for(split, 0, (size_t)slot_h * B * 2, &hi[0], &lo[0], &hp[0]));
+    CKS(planes_for(split, 1, (size_t)slot_h * B * 2, &hi[1], &lo[1], &hp[1]));
+    CKS(tmaps4_for(split ? hp[0] : hi[0], lo[0], N, B, ld_h, slot_h, m[0]));
+    CKS(tmaps4_for(split ? hp[1] : hi[1], lo[1], N, B, ld_h, slot_h, m[1]));
     A.ld_h = ld_h;
     A.slot_h = slot_h;
   } else {
@@ -1260,9 +1247,9 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
   CK(cudaMemcpyAsync(nal, (char*)h + pb + bb2, ab, cudaMemcpyHostToDevice, st));
   CK(cudaEventRecord(g.stage_done, st));
 
-  CUtensorMap mY[4], mY5[5], mG[2][4];
+  CUtensorMap mY[4], mY4[4], mG[2][4];
   CKS(tmaps_for(yh, yl, N, B, ld_h, slot_h, mY));
-  CKS(tmaps5_for(yhp, yl, yh, N, B, ld_h, slot_h, mY5));
+  CKS(tmaps4_for(split ? yhp : yh, yl, N, B, ld_h, slot_h, mY4));
   CKS(tmaps_for(gh[0], gl[0], N, B, ld_h, slot_h, mG[0]));
   CKS(tmaps_for(gh[1], gl[1], N, B, ld_h, slot_h, mG[1]));
   const float ls = std::ldexp(1.0f, g.lo_scale_exp);
@@ -1310,7 +1297,7 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
       F.ld_rn = N;
       F.lp = (const LayerParams*)params + (size_t)n * B;
       F.nseg = 1;
-      CK(launch_syrk_tc1(F, mY5, split, tgrid, st));
+      CK(launch_syrk_tc1(F, mY4, split, tgrid, st));
     }
     for (int n = n1 - 1; n >= n0; --n) {
       float* Yn = segY(n - n0);

@@ -1,9 +1,10 @@
 // Epilogue of the single-accumulator tcgen05 squaring kernels (syrk_tc1.cu,
 // syrk_tc2.cu).  Eight warps drain one 128 x 256 FP32 accumulator of
-// 2^s P = 2^s Y^2 (Eq. 14) from TMEM and apply the layer of Alg. 1,
+// 2^(2s) P = 2^(2s) Y^2 (Eq. 14) from TMEM and apply the layer of Alg. 1,
 //     Y' = ca Y + cb P + cc I        (S = alpha I + Y, Eq. 16 form)
 // with the diagonal in FP64 from the row norms (Y^2)_ii = sum_k Y_ik^2,
-// re-split Y' into the FP16 operands of the next layer (Eq. 12), store the
+// re-split Y' into the FP16 operand planes of the next layer (Eq. 12: hp =
+// 2^s hi and lo' for the split kernels, hi for plain FP16), store the
 // upper tile and its mirror, and publish the tile's FP64 (tr Y', ||Y'||_F^2)
 // partial.
 //
@@ -65,7 +66,8 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
   const int r = I * BN + h * BM + q * 32 + lane;
   const bool mirror = (I != J);
   const bool outD = (p.out_mode == OUT_D);
-  const float unscale = SPLIT ? a.lo_unscale : 1.f;
+  // split: the accumulator holds 2^(2s) P (both operand planes scaled by 2^s)
+  const float unscale = SPLIT ? a.lo_unscale * a.lo_unscale : 1.f;
   const float lo_scale = a.lo_scale;
   float* Y = a.Yout + (long long)b * a.slot_y;
   const float* Yold = a.Yin + (long long)b * a.slot_y;
@@ -179,8 +181,8 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
           for (int j = 0; j < 32; ++j)
             if (c0 + j < N) Y[(long long)r * ld + c0 + j] = y[j];
         }
-        if (ho && c0 + 32 <= (int)ldh) {
-          // 32 halves per part, packed in registers; columns >= N carry zeros
+        if ((ho || lo_ || hp_) && c0 + 32 <= (int)ldh) {
+          // 32 halves per plane, packed in registers; columns >= N carry zeros
           uint32_t ph[16], pl[16], pp[16];
 #pragma unroll
           for (int j2 = 0; j2 < 16; ++j2) {
@@ -191,9 +193,12 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
             pl[j2] = pack_h2(l0, l1);
             pp[j2] = pack_h2(__float2half_rn(__half2float(h0) * lo_scale), __float2half_rn(__half2float(h1) * lo_scale));
           }
-          uint4* dh = reinterpret_cast<uint4*>(ho + (long long)r * ldh + c0);
+          if (ho) {
+            uint4* dh = reinterpret_cast<uint4*>(ho + (long long)r * ldh + c0);
 #pragma unroll
-          for (int j4 = 0; j4 < 4; ++j4) dh[j4] = make_uint4(ph[4 * j4], ph[4 * j4 + 1], ph[4 * j4 + 2], ph[4 * j4 + 3]);
+            for (int j4 = 0; j4 < 4; ++j4)
+              dh[j4] = make_uint4(ph[4 * j4], ph[4 * j4 + 1], ph[4 * j4 + 2], ph[4 * j4 + 3]);
+          }
           if (lo_) {
             uint4* dl = reinterpret_cast<uint4*>(lo_ + (long long)r * ldh + c0);
 #pragma unroll
@@ -219,10 +224,10 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
             D[(long long)c * N + r] = y[j];
           } else {
             Y[(long long)c * ld + r] = y[j];
-            if (ho) {
+            if (ho || lo_ || hp_) {
               __half hh, ll;
               split_fp16(y[j], lo_scale, hh, ll);
-              ho[(long long)c * ldh + r] = hh;
+              if (ho) ho[(long long)c * ldh + r] = hh;
               if (lo_) lo_[(long long)c * ldh + r] = ll;
               if (hp_) hp_[(long long)c * ldh + r] = __float2half_rn(__half2float(hh) * lo_scale);
             }

@@ -23,9 +23,9 @@ struct SqArgs {
   const float* Yin;        // FFMA path: operand and old value (read-only)
   float* Yout;             // updated iterate (may equal Yin on the tensor-core path)
   long long ld_y, slot_y;
-  __half* hi_out;          // split of the updated iterate (nullptr: not written)
-  __half* lo_out;
-  __half* hp_out;          // 2^s * hi of the updated iterate (single-accumulator kernel), or nullptr
+  __half* hi_out;          // FP16 planes of the updated iterate, each written when set:
+  __half* lo_out;          //   hi = fp16(Y'), lo' = fp16(2^s (Y' - hi)),
+  __half* hp_out;          //   hp = 2^s hi (single-accumulator kernels)
   long long ld_h, slot_h;
   float* const* Dptr;      // [batch] device array of output pointers (OUT_D)
   const int* Ns;           // [batch]
@@ -81,9 +81,11 @@ cudaError_t launch_rownorm(const float* Y, long long ld_y, long long slot_y, con
                            cudaStream_t st);
 
 // Single-accumulator split squaring (tcgen05, double-buffered TMEM): the
-// three products 2^s hi hi + lo' hi + hi lo' go into one FP32 accumulator,
-// with hp = 2^s hi a third FP16 operand.  tmaps: {hp(A), lo(A), hi(A),
-// hi(B), lo(B)}; split = false: plain FP16, tmaps[2] = hi(A), tmaps[3] = hi(B).
+// three products hp hp + lo' hp + hp lo' = 2^(2s) (hi hi + lo hi + hi lo)
+// go into one FP32 accumulator (hp = 2^s hi, lo' = 2^s lo).  tmaps: {p0(A),
+// p1(A), p0(B), p1(B)} with p0 = hp, p1 = lo'; split = false: plain FP16
+// with p0 = hi (p1 unused).  The epilogue writes the planes whose output
+// pointers are set (hp_out and lo_out for split, hi_out for plain).
 cudaError_t launch_syrk_tc1(const SqArgs& a, const CUtensorMap* tmaps, bool split, int grid, cudaStream_t st);
 size_t syrk_tc1_smem_bytes(bool split);
 // The same kernel run by CTA pairs (clusters of 2) that share the B operand by

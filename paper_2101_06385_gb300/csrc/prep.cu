@@ -239,14 +239,16 @@ __global__ void __launch_bounds__(256) input_layer_kernel(const float* const* __
   const double diag_add = shift ? 0.0 : e_max * inv;
   double tr = 0.0, sq = 0.0;
   if (active) {
-    const int rows = (hi != nullptr) ? rows_pad : N;
-    const int cols = (hi != nullptr) ? cols_pad : N;
+    // FP16 planes: hi (plain), or hp = 2^s hi and lo' (split); hi may be absent
+    const bool halves = (hi != nullptr) || (hp != nullptr);
+    const int rows = halves ? rows_pad : N;
+    const int cols = halves ? cols_pad : N;
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
       const float* hrow = H + (long long)r * ld_in;
       float* yrow = Y + (long long)b * slot_y + (long long)r * ld_y;
       __half* hirow = hi ? hi + (long long)b * slot_h + (long long)r * ld_h : nullptr;
-      __half* lorow = (hi && lo) ? lo + (long long)b * slot_h + (long long)r * ld_h : nullptr;
-      __half* hprow = (hi && hp) ? hp + (long long)b * slot_h + (long long)r * ld_h : nullptr;
+      __half* lorow = (halves && lo) ? lo + (long long)b * slot_h + (long long)r * ld_h : nullptr;
+      __half* hprow = hp ? hp + (long long)b * slot_h + (long long)r * ld_h : nullptr;
       float sqf = 0.f;
       for (int col = threadIdx.x; col < cols; col += blockDim.x) {
         float y = 0.f;
@@ -258,10 +260,10 @@ __global__ void __launch_bounds__(256) input_layer_kernel(const float* const* __
           if (r == col) tr += (double)y;
           sqf = fmaf(y, y, sqf);
         }
-        if (hirow) {
+        if (halves) {
           __half h16, l16;
           split_fp16(y, lo_scale, h16, l16);
-          hirow[col] = h16;
+          if (hirow) hirow[col] = h16;
           if (lorow) lorow[col] = l16;
           if (hprow) hprow[col] = __float2half_rn(__half2float(h16) * lo_scale);
         }
@@ -406,14 +408,14 @@ __global__ void split_pad_kernel(const float* __restrict__ X, long long ld_x, lo
   for (long long gr = blockIdx.x; gr < rows; gr += gridDim.x) {
     const int b = (int)(gr / N), r = (int)(gr % N);
     const float* xr = X + (long long)b * slot_x + (long long)r * ld_x;
-    __half* hr = hi + (long long)b * slot_h + (long long)r * ld_h;
+    __half* hr = hi ? hi + (long long)b * slot_h + (long long)r * ld_h : nullptr;
     __half* lr = lo ? lo + (long long)b * slot_h + (long long)r * ld_h : nullptr;
     __half* pr = hp ? hp + (long long)b * slot_h + (long long)r * ld_h : nullptr;
     for (int c = threadIdx.x; c < (int)ld_h; c += blockDim.x) {
       const float x = (c < N) ? xr[c] : 0.f;
       __half h, l;
       split_fp16(x, lo_scale, h, l);
-      hr[c] = h;
+      if (hr) hr[c] = h;
       if (lr) lr[c] = l;
       if (pr) pr[c] = __float2half_rn(__half2float(h) * lo_scale);
     }

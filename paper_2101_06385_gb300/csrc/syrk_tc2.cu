@@ -9,17 +9,20 @@
 // super tile instead of twice.  A stage may be refilled only when both CTAs'
 // MMAs have released it (the release is a multicast commit).
 //
-// Alg. 2 / Eq. 14 with the low part scaled (Eq. 12, lo' = 2^s (Y - hi)):
-//     2^s P = hp hi + lo' hi + hi lo',     hp = 2^s hi (exact in FP16),
-// so all three products accumulate into ONE FP32 TMEM accumulator of
-// 128 x 256 (256 columns).  Two such accumulators fit in the 512 TMEM
+// Alg. 2 / Eq. 14 with both parts scaled by 2^s (Eq. 12: hi = fp16(Y),
+// lo' = fp16(2^s (Y - hi)); hp = 2^s hi is exact in FP16 for |Y| < 2^(15-s)):
+//     2^(2s) P = hp hp + lo' hp + hp lo',
+// so only two FP16 planes (hp, lo') are stored and loaded, and the three
+// products accumulate into ONE FP32 TMEM accumulator of 128 x 256 (256
+// columns).  Scaling by powers of two commutes with every rounding, so the
+// result equals that of the unscaled products hi hi + lo hi + hi lo.  Two such accumulators fit in the 512 TMEM
 // columns: while the epilogue warps drain tile t from one, the MMA issuer
 // fills the other with tile t+1, and the epilogue (FP32 update, re-split,
 // row and mirrored stores, traces) runs under the next tile's MMAs.
 //
 // CTA = 10 warps, persistent over the upper-tile list (one CTA per SM):
-//   warp 0      TMA producer (one thread): hp, lo', hi of the 128 A rows and
-//               hi, lo' of the 256 B rows per 64-wide K stage (112 KB, 2 stages)
+//   warp 0      TMA producer (one thread): hp, lo' of the 128 A rows and of
+//               the 256 B rows per 64-wide K stage (96 KB, 2 stages)
 //   warp 1      TMEM allocation + MMA issuer (one thread)
 //   warps 2..9  epilogue: TMEM lane quarter (warp % 4) x column half
 // Plain FP16 (split = false): hi hi only, 48 KB stages, 4 stages.
@@ -37,7 +40,7 @@ namespace tc2 {
 
 using namespace sp2::tc;
 
-constexpr int STAGE_SPLIT = 3 * A_BYTES + 2 * B_BYTES;  // 112 KB: hpA loA hiA hiB loB
+constexpr int STAGE_SPLIT = 2 * A_BYTES + 2 * B_BYTES;  // 96 KB: hpA loA hpB loB
 constexpr int STAGE_PLAIN = A_BYTES + B_BYTES;          // 48 KB: hiA hiB
 constexpr int STAGES_SPLIT = 2;
 constexpr int STAGES_PLAIN = 4;
@@ -45,9 +48,8 @@ constexpr int EPI_WARPS = epi::WARPS;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;  // two 256-column accumulators
 
-// stage offsets (split): hpA, loA, hiA (A_BYTES each), hiB, loB (B_BYTES each)
-constexpr int OFF_HPA = 0, OFF_LOA = A_BYTES, OFF_HIA = 2 * A_BYTES, OFF_HIB = 3 * A_BYTES,
-              OFF_LOB = 3 * A_BYTES + B_BYTES;
+// stage offsets (split): hpA, loA (A_BYTES each), hpB, loB (B_BYTES each)
+constexpr int OFF_HPA = 0, OFF_LOA = A_BYTES, OFF_HPB = 2 * A_BYTES, OFF_LOB = 2 * A_BYTES + B_BYTES;
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -81,9 +83,9 @@ __device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
 
 template <bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)
-    syrk_tc2_kernel(const __grid_constant__ CUtensorMap tm_hpA, const __grid_constant__ CUtensorMap tm_loA,
-                    const __grid_constant__ CUtensorMap tm_hiA, const __grid_constant__ CUtensorMap tm_hiB,
-                    const __grid_constant__ CUtensorMap tm_loB, const SqArgs a) {
+    syrk_tc2_kernel(const __grid_constant__ CUtensorMap tm_p0A, const __grid_constant__ CUtensorMap tm_p1A,
+                    const __grid_constant__ CUtensorMap tm_p0B, const __grid_constant__ CUtensorMap tm_p1B,
+                    const SqArgs a) {
   constexpr int STAGES = SPLIT ? STAGES_SPLIT : STAGES_PLAIN;
   constexpr int STAGE_BYTES = SPLIT ? STAGE_SPLIT : STAGE_PLAIN;
 
@@ -157,14 +159,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           mbar_expect_tx(&full[stage], STAGE_BYTES);
           const int k0 = kb * BK;
           if (SPLIT) {
-            tma_load_3d(st + OFF_HPA, &tm_hpA, k0, rowA, b, &full[stage]);
-            tma_load_3d(st + OFF_LOA, &tm_loA, k0, rowA, b, &full[stage]);
-            tma_load_3d(st + OFF_HIA, &tm_hiA, k0, rowA, b, &full[stage]);
-            tma_load_3d_mc(st + OFF_HIB + rank * (B_BYTES / 2), &tm_hiB, k0, rowB, b, &full[stage], 0x3);
-            tma_load_3d_mc(st + OFF_LOB + rank * (B_BYTES / 2), &tm_loB, k0, rowB, b, &full[stage], 0x3);
+            tma_load_3d(st + OFF_HPA, &tm_p0A, k0, rowA, b, &full[stage]);
+            tma_load_3d(st + OFF_LOA, &tm_p1A, k0, rowA, b, &full[stage]);
+            tma_load_3d_mc(st + OFF_HPB + rank * (B_BYTES / 2), &tm_p0B, k0, rowB, b, &full[stage], 0x3);
+            tma_load_3d_mc(st + OFF_LOB + rank * (B_BYTES / 2), &tm_p1B, k0, rowB, b, &full[stage], 0x3);
           } else {
-            tma_load_3d(st, &tm_hiA, k0, rowA, b, &full[stage]);
-            tma_load_3d_mc(st + A_BYTES + rank * (B_BYTES / 2), &tm_hiB, k0, rowB, b, &full[stage], 0x3);
+            tma_load_3d(st, &tm_p0A, k0, rowA, b, &full[stage]);
+            tma_load_3d_mc(st + A_BYTES + rank * (B_BYTES / 2), &tm_p0B, k0, rowB, b, &full[stage], 0x3);
           }
           ++armed[stage];
           if (++stage == STAGES) {
@@ -216,10 +217,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint32_t koff = ks * UMMA_K * 2;
             const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
             if (SPLIT) {
-              const uint64_t dhiB = make_desc_sw128(st + OFF_HIB + koff);
-              mma_f16(d, make_desc_sw128(st + OFF_HPA + koff), dhiB, acc);               // 2^s hi hi
-              mma_f16(d, make_desc_sw128(st + OFF_LOA + koff), dhiB, 1u);                // lo' hi
-              mma_f16(d, make_desc_sw128(st + OFF_HIA + koff), make_desc_sw128(st + OFF_LOB + koff), 1u);  // hi lo'
+              const uint64_t dhpA = make_desc_sw128(st + OFF_HPA + koff);
+              const uint64_t dhpB = make_desc_sw128(st + OFF_HPB + koff);
+              mma_f16(d, dhpA, dhpB, acc);                                       // hp hp
+              mma_f16(d, make_desc_sw128(st + OFF_LOA + koff), dhpB, 1u);        // lo' hp
+              mma_f16(d, dhpA, make_desc_sw128(st + OFF_LOB + koff), 1u);        // hp lo'
             } else {
               mma_f16(d, make_desc_sw128(st + koff), make_desc_sw128(st + A_BYTES + koff), acc);
             }
@@ -294,11 +296,11 @@ cudaError_t launch_syrk_tc2(const SqArgs& a, const CUtensorMap* tm, bool split, 
   if (split) {
     e = cudaFuncSetAttribute(tc2::syrk_tc2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<true>, tm[0], tm[1], tm[2], tm[3], tm[4], a);
+    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<true>, tm[0], tm[1], tm[2], tm[3], a);
   } else {
     e = cudaFuncSetAttribute(tc2::syrk_tc2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<false>, tm[0], tm[1], tm[2], tm[3], tm[4], a);
+    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<false>, tm[0], tm[1], tm[2], tm[3], a);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
