@@ -59,7 +59,8 @@ void set_err(const char* fmt, ...) {
 enum BufId {
   B_HI0, B_LO0, B_HI1, B_LO1, B_Y0, B_Y1, B_CTL, B_TILES, B_TOFF, B_TCNT, B_TPART, B_IDONE,
   B_PART, B_TICKET, B_ERR, B_DPTR, B_NS, B_HS, B_TRACES, B_PARAMS, B_BOUNDS, B_RN, B_PART2,
-  B_G, B_SEG, B_GH0, B_GL0, B_GH1, B_GL1, B_DOTS, B_TDOTS, B_PARAMS2, B_NALPHA, B_HP0, B_HP1, B_COUNT
+  B_G, B_SEG, B_GH0, B_GL0, B_GH1, B_GL1, B_DOTS, B_TDOTS, B_PARAMS2, B_NALPHA, B_HP0, B_HP1, B_RNP0, B_RNP1,
+  B_COUNT
 };
 
 struct Buf {
@@ -268,6 +269,23 @@ sp2_status planes_for(bool split, int k, size_t bytes, void** hi, void** lo, voi
     CKS(ws(k ? B_HI1 : B_HI0, bytes, hi));
   }
   return SP2_OK;
+}
+
+// Row-norm segment sums carried between the single-accumulator launches:
+// B instances of up to N rows, ceil(N / 32) segments each.
+sp2_status rnp_for(int N, int B, SqArgs& A, void** rnp) {
+  A.ld_rnp = round_up(N, 32);
+  A.slot_rnp = (long long)((N + 31) / 32) * A.ld_rnp;
+  CKS(ws(B_RNP0, (size_t)A.slot_rnp * B * sizeof(float), &rnp[0]));
+  CKS(ws(B_RNP1, (size_t)A.slot_rnp * B * sizeof(float), &rnp[1]));
+  return SP2_OK;
+}
+
+// Launch k of a device-driven loop reads the row norms of its input (the
+// FP64 ones of the input layer for k = 0) and writes those of its output.
+void rnp_step(SqArgs& A, void** rnp, int k) {
+  A.rnp_out = (float*)rnp[k & 1];
+  A.rnp_in = k > 0 ? (const float*)rnp[(k - 1) & 1] : nullptr;
 }
 
 void init_ctl(Ctl* c, int N, int n_occ, double tol, int max_iter) {
@@ -678,19 +696,23 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
     A.ld_h = ld_h;
     A.slot_h = slot_h;
     const int grid = std::min(ntiles, g.num_sms) & (g.pair_kernel ? ~1 : ~0);
+    // one launch per layer: the epilogue leaves the row norms of Y' for the
+    // next launch and the last tile runs the control step
+    void* rnp[2];
+    CKS(rnp_for(N, 1, A, rnp));
+    A.fused_ctl = 1;
     CK(cudaEventRecord(g.lev[0], st));
     for (int k = 0; k < max_iter + 2; ++k) {
       const int cur = k & 1;
       A.hi_out = (__half*)hi[cur ^ 1];
       A.lo_out = (__half*)lo[cur ^ 1];
       A.hp_out = (__half*)hp[cur ^ 1];
+      rnp_step(A, rnp, k);
       if (g.pair_kernel)
         CK(launch_syrk_tc2(A, m[cur], split, grid, st));
       else
         CK(launch_syrk_tc1(A, m[cur], split, grid, st));
       CK(cudaEventRecord(g.lsq[k], st));
-      CK(launch_rownorm(D_out, N, (long long)N * N, (const int*)ns, 1, N, (double*)rn, N, (Ctl*)ctl, (double2*)part,
-                        (unsigned*)tick, rgrid, st));
       CK(cudaEventRecord(g.lev[k + 1], st));
     }
   } else {
@@ -887,16 +909,18 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
     A.ld_h = ld_h;
     A.slot_h = slot_h;
     const int grid = std::min(nt, g.num_sms);
+    void* rnp[2];
+    CKS(rnp_for(Nmax, B, A, rnp));
+    A.fused_ctl = 1;
     CK(cudaEventRecord(g.lev[0], st));
     for (int k = 0; k < max_iter + 2; ++k) {
       const int cur = k & 1;
       A.hi_out = (__half*)hi[cur ^ 1];
       A.lo_out = (__half*)lo[cur ^ 1];
       A.hp_out = (__half*)hp[cur ^ 1];
+      rnp_step(A, rnp, k);
       CK(launch_syrk_tc1(A, m[cur], split, grid, st));
       CK(cudaEventRecord(g.lsq[k], st));
-      CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
-                        (double2*)part, (unsigned*)tick, rgrid, st));
       CK(cudaEventRecord(g.lev[k + 1], st));
     }
   } else {
@@ -1136,10 +1160,14 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
                         g.shift, 0, B, igrid, st));
   if (ckpt)
     CK(launch_materialize((float*)Y[0], N, slot, N, B, (const double*)alpha, ckpt_slot(0), N, slot, mgrid, st));
+  void* rnp[2] = {nullptr, nullptr};
+  if (tc) CKS(rnp_for(N, B, A, rnp));
   for (int n = 0; n < L; ++n) {
     const int cur = n & 1;
     float* Yc = (float*)Y[tc ? 0 : cur];
-    CK(launch_rownorm(Yc, N, slot, (const int*)ns, B, N, (double*)rn, N, nullptr, nullptr, nullptr, rgrid, st));
+    // tensor-core layers carry the row norms from one launch to the next
+    if (!tc || n == 0)
+      CK(launch_rownorm(Yc, N, slot, (const int*)ns, B, N, (double*)rn, N, nullptr, nullptr, nullptr, rgrid, st));
     A.lp = (const LayerParams*)params + (size_t)n * B;
     if (tc) {
       A.Yin = X_out;
@@ -1147,6 +1175,7 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
       A.hi_out = (__half*)hi[cur ^ 1];
       A.lo_out = (__half*)lo[cur ^ 1];
       A.hp_out = (__half*)hp[cur ^ 1];
+      rnp_step(A, rnp, n);
       CK(launch_syrk_tc1(A, m[cur], split, std::min(ntiles, g.num_sms), st));
     } else {
       A.Yin = Yc;

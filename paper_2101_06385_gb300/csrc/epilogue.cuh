@@ -49,6 +49,46 @@ __device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
   return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
+// (Y^2)_rr = sum_k Y_rk^2 of the input iterate: from the FP64 row norms, or
+// summed in FP64 from the FP32 segment sums the previous launch left (eight
+// accumulators over interleaved segments, combined in a fixed order).
+__device__ __forceinline__ double row_norm(const SqArgs& a, int b, int N, int r) {
+  if (!a.rnp_in) return a.rn ? a.rn[(long long)b * a.ld_rn + r] : 0.0;
+  const float* p = a.rnp_in + (long long)b * a.slot_rnp + r;
+  const int nseg = (N + 31) >> 5;
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int s = 0;
+  for (; s + 8 <= nseg; s += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] += (double)p[(long long)(s + u) * a.ld_rnp];
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    if (s + u < nseg) acc[u] += (double)p[(long long)(s + u) * a.ld_rnp];
+  return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+}
+
+// Lane L returns sum over the 32 lanes of y[L]^2 (lanes with valid == false
+// contribute zero): a butterfly that halves the values held per lane at each
+// of the five exchange steps (31 shuffles).
+__device__ __forceinline__ float column_sums_sq(const float (&y)[32], bool valid) {
+  const int lane = threadIdx.x & 31;
+  float s[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) s[j] = valid ? y[j] * y[j] : 0.f;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool upper = (lane & w) != 0;
+#pragma unroll
+    for (int k = 0; k < w; ++k) {
+      const float send = upper ? s[k] : s[k + w];
+      const float keep = upper ? s[k + w] : s[k];
+      s[k] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return s[0];
+}
+
 // Tile t with accumulator use `it` (buffer it & 1).  Returns 0 when the
 // tile's instance is inactive (nothing issued for it), 1 when done, -1 when
 // the accumulator wait failed.
@@ -77,7 +117,8 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
   // the old row segment (into L2)
   double rn_r = 0.0;
   if (r < N) {
-    if (!mirror && a.rn) rn_r = a.rn[(long long)b * a.ld_rn + r];
+    const int dcol = r - (J * BN + hc * 128);
+    if (!mirror && (unsigned)dcol < 128u) rn_r = row_norm(a, b, N, r);
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
       const int c0 = J * BN + hc * 128 + ch * 32;
@@ -94,6 +135,7 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
   }
   tc_fence_after();
 
+  float* rnp = a.rnp_out ? a.rnp_out + (long long)b * a.slot_rnp : nullptr;
   __half* ho = a.hi_out ? a.hi_out + (long long)b * a.slot_h : nullptr;
   __half* lo_ = a.lo_out ? a.lo_out + (long long)b * a.slot_h : nullptr;
   __half* hp_ = a.hp_out ? a.hp_out + (long long)b * a.slot_h : nullptr;
@@ -120,7 +162,10 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
     const int jd = r - c0;
     const bool dchunk = !mirror && (unsigned)jd < 32u;
     float y[32];
-    if (r < N) {
+    if (r >= N) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) y[j] = 0.f;
+    } else {
       const bool full_chunk = (c0 + 32 <= N) && vec_y;
       if (full_chunk) {
         const float4* src = reinterpret_cast<const float4*>(Yold + (long long)r * ld + c0);
@@ -154,7 +199,7 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       // one FP64 update per row, outside the unrolled element loop
       float ydo = 0.f;
       if (dchunk) {
-        const double pd = a.rn ? rn_r : (double)p_d;
+        const double pd = (a.rn || a.rnp_in) ? rn_r : (double)p_d;
         const double yd = p.ca_d * (double)yold_d + p.cb_d * pd + p.cc_d;
         tr += yd;
         const float ydf = (float)yd;
@@ -167,6 +212,7 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
 #pragma unroll
       for (int j = 0; j < 32; ++j) sqf = fmaf(y[j], y[j], sqf);
       sq += (double)sqf;
+      if (rnp && c0 < N) rnp[(long long)(c0 >> 5) * a.ld_rnp + r] = sqf;
       if (outD) {
 #pragma unroll
         for (int j = 0; j < 32; ++j)
@@ -213,6 +259,12 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
           }
         }
       }
+    }
+    // row norms of the mirror: rows c0 + j of Y' get the segment of the 32
+    // rows of this warp, the column sums of y^2 over the lanes
+    if (mirror && rnp) {
+      const float cs = column_sums_sq(y, r < N);
+      if (c0 + lane < N) rnp[(long long)((I * BN + h * BM + q * 32) >> 5) * a.ld_rnp + c0 + lane] = cs;
     }
     // mirrored store: lanes hold consecutive rows r -> consecutive columns
     if (mirror && r < N) {

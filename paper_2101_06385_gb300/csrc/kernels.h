@@ -41,6 +41,17 @@ struct SqArgs {
   double* traces_out;      // [batch][2] when ctl == nullptr, or nullptr
   const double* rn;        // [batch][ld_rn] FP64 row norms sum_k Y[r][k]^2 = (Y^2)_rr of the input
   long long ld_rn;
+  // Row norms carried between launches (single-accumulator kernels): FP32
+  // sums of squares of 32-column segments, rnp[b][seg][row] at
+  // b * slot_rnp + seg * ld_rnp + row.  rnp_out receives those of Y' (every
+  // (row, segment) once: the direct part of an upper tile or the column sums
+  // of its mirror); rnp_in, when set, holds those of the input Y and replaces
+  // rn: (Y^2)_rr = sum over segments in FP64.
+  float* rnp_out;
+  const float* rnp_in;
+  long long ld_rnp, slot_rnp;
+  int fused_ctl;           // 1: the last tile of an instance runs its control step with
+                           //    (tr Y', ||Y'||_F^2) from the tiles (no row-norm launch)
   int nseg;                // 1: P = Y Y (one operand); 2: P = A B^T + B A^T (second map set)
   const float* aux;        // adjoint mode: Y_n, same layout as Yin; dots <P, aux>, <Yin, aux>
   double* tile_dots;       // [ntiles][3] per-tile (tr Yin, <Yin, aux>, <P, aux>) in adjoint mode

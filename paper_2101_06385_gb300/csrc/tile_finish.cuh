@@ -10,9 +10,9 @@
 namespace sp2 {
 
 // Warp-collective: all 32 lanes of one warp call it; (tr, sq) valid in lane 0.
-// With a control block: a final (OUT_D) launch completes the solve here;
-// otherwise tr Y' is left for the row-norm launch, which owns the exact
-// ||Y'||_F^2 and runs the control step.
+// With a control block: a final (OUT_D) launch, or any launch with fused_ctl
+// set, runs the control step here; otherwise tr Y' is left for the row-norm
+// launch, which owns ||Y'||_F^2 and runs the control step.
 __device__ inline void finish_tile_warp(const SqArgs& a, int t, int b, double tr, double sq, int out_mode) {
   const int lane = threadIdx.x & 31;
   unsigned last = 0;
@@ -55,7 +55,7 @@ __device__ inline void finish_tile_warp(const SqArgs& a, int t, int b, double tr
     }
     a.inst_done[b] = 0u;
     if (a.ctl) {
-      if (out_mode == OUT_D)
+      if (out_mode == OUT_D || a.fused_ctl)
         control_step(a.ctl + b, T, Q);
       else
         a.ctl[b].trY_new = T;
