@@ -1,12 +1,14 @@
 // C ABI of libsp2.so: argument checks, workspace, launch sequences.
 //
 // A call of sp2_density_matrix enqueues, on the library stream:
-//   K1 Gershgorin bounds -> K2 input layer + split + first control step ->
-//   (max_iter + 2) squaring launches.  Each squaring launch reads the layer
-//   coefficients that the previous launch's control step left on the device
-//   and does nothing once the solve has finished, so no host round trip is
-//   needed inside the loop.  The two launches after the loop's last layer
-//   are the refinement of Eq. 15; the last one writes D_out.
+//   K1 Gershgorin bounds -> K2 input layer + split -> FP64 row norms of Y_0
+//   and the first control step -> (max_iter + 2) squaring launches.  Each
+//   squaring launch reads the layer coefficients that the previous launch's
+//   control step left on the device, leaves the row norms of its output for
+//   the next one, runs the control step in its last tile, and does nothing
+//   once the solve has finished, so no host round trip is needed inside the
+//   loop.  The two launches after the loop's last layer are the refinement of
+//   Eq. 15; the last one writes D_out.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>

@@ -15,8 +15,8 @@ constexpr int BM = kTcBM;           // 128
 constexpr int BN = kTcBN;           // 256
 constexpr int BK = 64;              // K per stage: 64 FP16 = 128 B rows (128-byte swizzle)
 constexpr int UMMA_K = 16;          // K per tcgen05.mma (kind::f16)
-constexpr int A_BYTES = BM * BK * 2;   // 8 KB
-constexpr int B_BYTES = BN * BK * 2;   // 16 KB
+constexpr int A_BYTES = BM * BK * 2;   // 16 KB
+constexpr int B_BYTES = BN * BK * 2;   // 32 KB
 constexpr unsigned long long kTimeoutNs = 4000000000ull;  // 4 s
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = F16
