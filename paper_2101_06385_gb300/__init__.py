@@ -14,6 +14,7 @@ import os
 import re
 from typing import List, Optional, Sequence, Tuple
 
+import numpy as np
 import torch
 
 from ._build import LIB as _LIB_PATH
@@ -175,6 +176,7 @@ def init(device: int = 0, precision: str = "split", lo_scale_exp: int = 11, shif
     cfg = _Config(device, None, PRECISIONS[precision], lo_scale_exp, 1 if shift_identity else 0, eps_bias)
     _check(lib.sp2_init(ctypes.byref(cfg)))
     _state["device"] = device
+    _state["precision"] = precision
 
 
 def finalize() -> None:
@@ -183,8 +185,28 @@ def finalize() -> None:
 
 
 def set_precision(precision: str) -> None:
+    """Library-wide arithmetic of the squarings: "split", "fp16" or "fp32"."""
     _ensure_init(None)
     _check(_load().sp2_set_precision(PRECISIONS[precision]))
+    _state["precision"] = precision
+
+
+class _precision:
+    """A per-call precision: switched in for one call, the library-wide one
+    restored afterwards."""
+
+    def __init__(self, precision: Optional[str]):
+        self.p = precision
+
+    def __enter__(self):
+        if self.p is not None:
+            self.old = _state.get("precision", "split")
+            _check(_load().sp2_set_precision(PRECISIONS[self.p]))
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            _load().sp2_set_precision(PRECISIONS[self.old])
+        return False
 
 
 def _ensure_init(t: Optional[torch.Tensor]) -> None:
@@ -210,6 +232,34 @@ def _stats(s: _Stats, status: int) -> Stats:
                  square_ms=[float(v) for v in s.square_ms[:s.launches]])
 
 
+def _stats_many(st, B: int) -> List[Stats]:
+    """Stats of a batched call, read column-wise through one structured-array
+    view of the ctypes records (per-element ctypes access would dominate)."""
+    a = np.ctypeslib.as_array(st)
+    col = {k: a[k].tolist() for k in ("iterations", "launches", "converged_by", "e_min", "e_max", "idemp_err",
+                                       "trace", "alpha", "time_ms", "flops_alg", "prologue_ms")}
+    nmax = max(col["iterations"]) if B else 0
+    lmax = max(col["launches"]) if B else 0
+    sig = a["sigma"][:, :nmax].tolist()
+    ide = a["iderr"][:, :nmax].tolist()
+    # per-launch times are shared by the instances of one call: convert once
+    la, sa = a["layer_ms"][:, :lmax], a["square_ms"][:, :lmax]
+    if B and (la == la[0]).all() and (sa == sa[0]).all():
+        lms, sms = [la[0].tolist()] * B, [sa[0].tolist()] * B
+    else:
+        lms, sms = la.tolist(), sa.tolist()
+    out = []
+    for i in range(B):
+        n, nl, c = col["iterations"][i], col["launches"][i], col["converged_by"][i]
+        out.append(Stats(status=1 if c == 4 else 0, iterations=n, converged_by=_STOP.get(c, str(c)),
+                         e_min=col["e_min"][i], e_max=col["e_max"][i], idemp_err=col["idemp_err"][i],
+                         trace=col["trace"][i], alpha=col["alpha"][i], time_ms=col["time_ms"][i],
+                         flops_alg=col["flops_alg"][i], sigmas=sig[i][:n], iderr=ide[i][:n],
+                         prologue_ms=col["prologue_ms"][i], launches=nl, layer_ms=lms[i][:nl],
+                         square_ms=sms[i][:nl]))
+    return out
+
+
 def density_matrix(H: torch.Tensor, n_occ: int, tol: float = 0.0, max_iter: int = 100,
                    out: Optional[torch.Tensor] = None, precision: Optional[str] = None,
                    sync: bool = True) -> Tuple[torch.Tensor, Optional[Stats]]:
@@ -223,14 +273,13 @@ def density_matrix(H: torch.Tensor, n_occ: int, tol: float = 0.0, max_iter: int 
         raise ValueError("H must be square")
     _ensure_init(H)
     lib = _load()
-    if precision is not None:
-        _check(lib.sp2_set_precision(PRECISIONS[precision]))
     N = H.shape[0]
     D = out if out is not None else torch.empty_like(H)
     _dev_f32(D, "out")
     st = _Stats()
-    status = lib.sp2_density_matrix(H.data_ptr(), N, int(n_occ), float(tol), int(max_iter), D.data_ptr(),
-                                    ctypes.byref(st) if sync else None)
+    with _precision(precision):
+        status = lib.sp2_density_matrix(H.data_ptr(), N, int(n_occ), float(tol), int(max_iter), D.data_ptr(),
+                                        ctypes.byref(st) if sync else None)
     _check(status, allow=(0, 1))
     return D, (_stats(st, status) if sync else None)
 
@@ -246,15 +295,25 @@ def density_matrix_batched(Hs: Sequence[torch.Tensor], n_occ: Sequence[int], tol
     _ensure_init(Hs[0])
     lib = _load()
     B = len(Hs)
-    Ds = list(outs) if outs is not None else [torch.empty_like(h) for h in Hs]
+    sizes = [h.shape[0] for h in Hs]
+    if outs is not None:
+        Ds = list(outs)
+    else:
+        # one allocation for all outputs, returned as views (64-element aligned offsets)
+        offs, o = [], 0
+        for n in sizes:
+            offs.append(o)
+            o += (n * n + 63) // 64 * 64
+        flat = torch.empty(o, dtype=torch.float32, device=Hs[0].device)
+        Ds = [flat[off:off + n * n].view(n, n) for off, n in zip(offs, sizes)]
     hp = (ctypes.c_void_p * B)(*[h.data_ptr() for h in Hs])
     dp = (ctypes.c_void_p * B)(*[d.data_ptr() for d in Ds])
-    ns = (ctypes.c_int * B)(*[h.shape[0] for h in Hs])
+    ns = (ctypes.c_int * B)(*sizes)
     no = (ctypes.c_int * B)(*[int(x) for x in n_occ])
     st = (_Stats * B)()
     status = lib.sp2_density_matrix_batched(hp, ns, no, B, float(tol), int(max_iter), dp, st if sync else None)
     _check(status, allow=(0, 1))
-    return Ds, ([_stats(st[i], 1 if st[i].converged_by == 4 else 0) for i in range(B)] if sync else None)
+    return Ds, (_stats_many(st, B) if sync else None)
 
 
 def gershgorin(H: torch.Tensor) -> Tuple[float, float]:
@@ -282,14 +341,13 @@ def layer(X: torch.Tensor, a: float, b: float, c: float, precision: Optional[str
     _dev_f32(X, "X")
     _ensure_init(X)
     lib = _load()
-    if precision is not None:
-        _check(lib.sp2_set_precision(PRECISIONS[precision]))
     Xb = X if X.dim() == 3 else X.unsqueeze(0)
     B, N = Xb.shape[0], Xb.shape[-1]
     out = torch.empty_like(Xb)
     tr = (ctypes.c_double * (2 * B))()
-    _check(lib.sp2_layer(Xb.data_ptr(), B, N, float(a), float(b), float(c), out.data_ptr(),
-                         tr if traces else None))
+    with _precision(precision):
+        _check(lib.sp2_layer(Xb.data_ptr(), B, N, float(a), float(b), float(c), out.data_ptr(),
+                             tr if traces else None))
     out = out if X.dim() == 3 else out[0]
     if not traces:
         return out, None

@@ -93,6 +93,12 @@ struct State {
   // squaring kernel of the single-matrix solve: CTA pairs sharing B through
   // TMA multicast (default) or single CTAs (SP2_SQUARE_KERNEL=single)
   bool pair_kernel = true;
+  // the batched solve's launch sequence as an instantiated CUDA graph, and
+  // what was baked into it (SP2_GRAPHS=0 enqueues the launches directly)
+  bool use_graphs = true;
+  cudaGraphExec_t bgraph = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<uint64_t> bgraph_key;
 };
 
 State g;
@@ -397,6 +403,8 @@ sp2_status sp2_init(const sp2_config* cfg) {
   {
     const char* kv = getenv("SP2_SQUARE_KERNEL");
     g.pair_kernel = !(kv && strcmp(kv, "single") == 0);
+    const char* gv = getenv("SP2_GRAPHS");
+    g.use_graphs = !(gv && strcmp(gv, "0") == 0);
   }
   g.device = c.device;
   g.stream = (cudaStream_t)c.stream;
@@ -429,6 +437,11 @@ sp2_status sp2_finalize(void) {
     if (i < SP2_MAX_LAYERS && g.lsq[i]) cudaEventDestroy(g.lsq[i]);
     if (i < SP2_MAX_LAYERS) g.lsq[i] = nullptr;
   }
+  if (g.bgraph) cudaGraphExecDestroy(g.bgraph);
+  g.bgraph = nullptr;
+  if (g.cap_stream) cudaStreamDestroy(g.cap_stream);
+  g.cap_stream = nullptr;
+  g.bgraph_key.clear();
   g.tiles_key_N = -1;
   g.init = false;
   return SP2_OK;
@@ -835,8 +848,8 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
                        2 * B * sizeof(void*) + 64;
   void* h;
   CKS(staging(bytes, &h));
-  uint8_t* hp = (uint8_t*)h;
-  Ctl* hc = (Ctl*)hp;
+  uint8_t* hbuf = (uint8_t*)h;
+  Ctl* hc = (Ctl*)hbuf;
   for (int b = 0; b < B; ++b) init_ctl(hc + b, N[b], N_occ[b], tol, max_iter);
   const void** hh = (const void**)(hc + B);
   void** hd = (void**)(hh + B);
@@ -878,75 +891,128 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   A.lo_unscale = std::ldexp(1.0f, -g.lo_scale_exp);
   A.err = (int*)err;
 
-  CK(cudaEventRecord(g.ev0, st));
-  CK(launch_gershgorin_batched((const float* const*)hs, (const int*)ns, (Ctl*)ctl, B, (double2*)part, (unsigned*)tick,
-                               ggrid, st));
-  // iterate Y in uniform slots [B][Nmax][ld_y]; D_out[b] is written by the last layer
+  // workspace and tensor maps first: the launch sequence below makes only
+  // stream operations, so it can be captured into a CUDA graph
   const long long ld_y = round_up(Nmax, 4), slot_y = ld_y * Nmax;
+  const long long ld_h = round_up(Nmax, 64), slot_h = ld_h * Nmax;
   void* Y[2] = {nullptr, nullptr};
+  void *hi[2] = {nullptr, nullptr}, *lo[2] = {nullptr, nullptr}, *hp[2] = {nullptr, nullptr};
+  void* rnp[2] = {nullptr, nullptr};
+  CUtensorMap m[2][4];
   CKS(ws(B_Y0, (size_t)slot_y * B * 4, &Y[0]));
   if (tc) {
-    const long long ld_h = round_up(Nmax, 64), slot_h = ld_h * Nmax;
-    void *hi[2], *lo[2], *hp[2];
     CKS(planes_for(split, 0, (size_t)slot_h * B * 2, &hi[0], &lo[0], &hp[0]));
     CKS(planes_for(split, 1, (size_t)slot_h * B * 2, &hi[1], &lo[1], &hp[1]));
-    // Slots are Nmax x Nmax in the tensor maps: everything outside instance b's
-    // N_b x N_b block must read as zero.  The input layer zero-fills buffer 0's
-    // slot; the epilogues never write outside N_b x N_b (row tails up to the
-    // 32-column chunk are written as zeros), so buffer 1 is cleared here.
-    for (void* pl : {hi[1], lo[1], hp[1]})
-      if (pl) CK(cudaMemsetAsync(pl, 0, (size_t)slot_h * B * 2, st));
-    CK(launch_input_layer((const float* const*)hs, (const int*)ns, 0, (float*)Y[0], ld_y, slot_y, (__half*)hi[0],
-                          (__half*)lo[0], (__half*)hp[0], ld_h, slot_h, Nmax, (int)ld_h, A.lo_scale, (Ctl*)ctl, nullptr,
-                          (double2*)part, (unsigned*)tick, g.shift, 1, B, igrid, st));
-    CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
-                      (double2*)part, (unsigned*)tick, rgrid, st));
-    CUtensorMap m[2][4];
     CKS(tmaps4_for(split ? hp[0] : hi[0], lo[0], Nmax, B, ld_h, slot_h, m[0]));
     CKS(tmaps4_for(split ? hp[1] : hi[1], lo[1], Nmax, B, ld_h, slot_h, m[1]));
+    CKS(rnp_for(Nmax, B, A, rnp));
     A.Yin = (float*)Y[0];
     A.Yout = (float*)Y[0];
-    A.ld_y = ld_y;
-    A.slot_y = slot_y;
     A.ld_h = ld_h;
     A.slot_h = slot_h;
-    const int grid = std::min(nt, g.num_sms);
-    void* rnp[2];
-    CKS(rnp_for(Nmax, B, A, rnp));
     A.fused_ctl = 1;
-    CK(cudaEventRecord(g.lev[0], st));
-    for (int k = 0; k < max_iter + 2; ++k) {
-      const int cur = k & 1;
-      A.hi_out = (__half*)hi[cur ^ 1];
-      A.lo_out = (__half*)lo[cur ^ 1];
-      A.hp_out = (__half*)hp[cur ^ 1];
-      rnp_step(A, rnp, k);
-      CK(launch_syrk_tc1(A, m[cur], split, grid, st));
-      CK(cudaEventRecord(g.lsq[k], st));
-      CK(cudaEventRecord(g.lev[k + 1], st));
-    }
   } else {
     CKS(ws(B_Y1, (size_t)slot_y * B * 4, &Y[1]));
-    CK(launch_input_layer((const float* const*)hs, (const int*)ns, 0, (float*)Y[0], ld_y, slot_y, nullptr, nullptr, nullptr, 0,
-                          0, Nmax, Nmax, A.lo_scale, (Ctl*)ctl, nullptr, (double2*)part, (unsigned*)tick, g.shift, 1,
-                          B, igrid, st));
-    CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
-                      (double2*)part, (unsigned*)tick, rgrid, st));
-    A.ld_y = ld_y;
-    A.slot_y = slot_y;
-    CK(cudaEventRecord(g.lev[0], st));
-    for (int k = 0; k < max_iter + 2; ++k) {
-      const int cur = k & 1;
-      A.Yin = (float*)Y[cur];
-      A.Yout = (float*)Y[cur ^ 1];
-      CK(launch_syrk_simt(A, std::min(nt, 65535), st));
-      CK(cudaEventRecord(g.lsq[k], st));
-      CK(launch_rownorm((float*)Y[cur ^ 1], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
-                        (double2*)part, (unsigned*)tick, rgrid, st));
-      CK(cudaEventRecord(g.lev[k + 1], st));
-    }
   }
-  CK(cudaEventRecord(g.ev1, st));
+  A.ld_y = ld_y;
+  A.slot_y = slot_y;
+
+  // event records become graph nodes only with the external flag, which is
+  // valid during capture alone
+  auto enqueue = [&](cudaStream_t st, bool capturing) -> sp2_status {
+    const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    CK(cudaEventRecordWithFlags(g.ev0, st, evf));
+    CK(launch_gershgorin_batched((const float* const*)hs, (const int*)ns, (Ctl*)ctl, B, (double2*)part,
+                                 (unsigned*)tick, ggrid, st));
+    if (tc) {
+      // Slots are Nmax x Nmax in the tensor maps: everything outside instance
+      // b's N_b x N_b block must read as zero.  The input layer zero-fills
+      // buffer 0's slot; the epilogues never write outside N_b x N_b (row
+      // tails up to the 32-column chunk are written as zeros), so buffer 1 is
+      // cleared here.
+      for (void* pl : {hi[1], lo[1], hp[1]})
+        if (pl) CK(cudaMemsetAsync(pl, 0, (size_t)slot_h * B * 2, st));
+      CK(launch_input_layer((const float* const*)hs, (const int*)ns, 0, (float*)Y[0], ld_y, slot_y, (__half*)hi[0],
+                            (__half*)lo[0], (__half*)hp[0], ld_h, slot_h, Nmax, (int)ld_h, A.lo_scale, (Ctl*)ctl,
+                            nullptr, (double2*)part, (unsigned*)tick, g.shift, 1, B, igrid, st));
+      CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
+                        (double2*)part, (unsigned*)tick, rgrid, st));
+      const int grid = std::min(nt, g.num_sms);
+      CK(cudaEventRecordWithFlags(g.lev[0], st, evf));
+      for (int k = 0; k < max_iter + 2; ++k) {
+        const int cur = k & 1;
+        A.hi_out = (__half*)hi[cur ^ 1];
+        A.lo_out = (__half*)lo[cur ^ 1];
+        A.hp_out = (__half*)hp[cur ^ 1];
+        rnp_step(A, rnp, k);
+        CK(launch_syrk_tc1(A, m[cur], split, grid, st));
+        CK(cudaEventRecordWithFlags(g.lsq[k], st, evf));
+        CK(cudaEventRecordWithFlags(g.lev[k + 1], st, evf));
+      }
+    } else {
+      CK(launch_input_layer((const float* const*)hs, (const int*)ns, 0, (float*)Y[0], ld_y, slot_y, nullptr, nullptr,
+                            nullptr, 0, 0, Nmax, Nmax, A.lo_scale, (Ctl*)ctl, nullptr, (double2*)part,
+                            (unsigned*)tick, g.shift, 1, B, igrid, st));
+      CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
+                        (double2*)part, (unsigned*)tick, rgrid, st));
+      CK(cudaEventRecordWithFlags(g.lev[0], st, evf));
+      for (int k = 0; k < max_iter + 2; ++k) {
+        const int cur = k & 1;
+        A.Yin = (float*)Y[cur];
+        A.Yout = (float*)Y[cur ^ 1];
+        CK(launch_syrk_simt(A, std::min(nt, 65535), st));
+        CK(cudaEventRecordWithFlags(g.lsq[k], st, evf));
+        CK(launch_rownorm((float*)Y[cur ^ 1], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
+                          (double2*)part, (unsigned*)tick, rgrid, st));
+        CK(cudaEventRecordWithFlags(g.lev[k + 1], st, evf));
+      }
+    }
+    CK(cudaEventRecordWithFlags(g.ev1, st, evf));
+    return SP2_OK;
+  };
+
+  // The whole sequence replays as one CUDA graph while everything baked into
+  // it (sizes, grids, workspace addresses, stream) is unchanged; the per-call
+  // records (control blocks, pointers, tile list) were uploaded above.
+  if (g.use_graphs) {
+    const uint64_t key[] = {(uint64_t)B, (uint64_t)Nmax, (uint64_t)nt, (uint64_t)max_iter, (uint64_t)prec,
+                            (uint64_t)g.shift, (uint64_t)g.lo_scale_exp, (uint64_t)igrid, (uint64_t)rgrid,
+                            (uint64_t)ggrid, (uint64_t)g.num_sms, (uint64_t)(uintptr_t)st,
+                            (uint64_t)(uintptr_t)hs, (uint64_t)(uintptr_t)ns, (uint64_t)(uintptr_t)ctl,
+                            (uint64_t)(uintptr_t)dt, (uint64_t)(uintptr_t)doff, (uint64_t)(uintptr_t)dcnt,
+                            (uint64_t)(uintptr_t)dpart, (uint64_t)(uintptr_t)ddone, (uint64_t)(uintptr_t)err,
+                            (uint64_t)(uintptr_t)part, (uint64_t)(uintptr_t)tick, (uint64_t)(uintptr_t)rn,
+                            (uint64_t)(uintptr_t)Y[0], (uint64_t)(uintptr_t)Y[1], (uint64_t)(uintptr_t)hi[0],
+                            (uint64_t)(uintptr_t)hi[1], (uint64_t)(uintptr_t)lo[0], (uint64_t)(uintptr_t)lo[1],
+                            (uint64_t)(uintptr_t)hp[0], (uint64_t)(uintptr_t)hp[1], (uint64_t)(uintptr_t)rnp[0],
+                            (uint64_t)(uintptr_t)rnp[1]};
+    std::vector<uint64_t> kv(key, key + sizeof(key) / sizeof(key[0]));
+    if (!g.bgraph || g.bgraph_key != kv) {
+      if (g.bgraph) {
+        CK(cudaGraphExecDestroy(g.bgraph));
+        g.bgraph = nullptr;
+      }
+      // captured on the library's own stream (the legacy default stream
+      // cannot capture), launched on the caller's
+      if (!g.cap_stream) CK(cudaStreamCreateWithFlags(&g.cap_stream, cudaStreamNonBlocking));
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(g.cap_stream, cudaStreamCaptureModeThreadLocal));
+      const sp2_status se = enqueue(g.cap_stream, true);
+      const cudaError_t ce = cudaStreamEndCapture(g.cap_stream, &graph);
+      if (se != SP2_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return se;
+      }
+      CK(ce);
+      const cudaError_t ie = cudaGraphInstantiate(&g.bgraph, graph, 0);
+      cudaGraphDestroy(graph);
+      CK(ie);
+      g.bgraph_key = kv;
+    }
+    CK(cudaGraphLaunch(g.bgraph, st));
+  } else {
+    CKS(enqueue(st, false));
+  }
   if (!stats) return SP2_OK;
 
   void* hb;

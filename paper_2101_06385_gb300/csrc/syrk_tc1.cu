@@ -223,6 +223,22 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 }  // namespace tc1
 
+// The dynamic shared-memory opt-in, once per kernel and device (not a stream
+// operation, and kept out of captured launch sequences).
+namespace {
+template <typename K>
+cudaError_t set_smem_once(K kernel, int bytes, int which) {
+  static int done_dev[2] = {-1, -1};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (done_dev[which] == dev) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done_dev[which] = dev;
+  return e;
+}
+}  // namespace
+
 size_t syrk_tc1_smem_bytes(bool split) {
   const int stages = split ? tc1::STAGES_SPLIT : tc1::STAGES_PLAIN;
   const int sb = split ? tc1::STAGE_SPLIT : tc1::STAGE_PLAIN;
@@ -233,11 +249,11 @@ cudaError_t launch_syrk_tc1(const SqArgs& a, const CUtensorMap* tm, bool split, 
   const size_t smem = syrk_tc1_smem_bytes(split);
   cudaError_t e;
   if (split) {
-    e = cudaFuncSetAttribute(tc1::syrk_tc1_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_smem_once(tc1::syrk_tc1_kernel<true>, (int)smem, 1);
     if (e != cudaSuccess) return e;
     tc1::syrk_tc1_kernel<true><<<grid, tc1::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], a);
   } else {
-    e = cudaFuncSetAttribute(tc1::syrk_tc1_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_smem_once(tc1::syrk_tc1_kernel<false>, (int)smem, 0);
     if (e != cudaSuccess) return e;
     tc1::syrk_tc1_kernel<false><<<grid, tc1::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], a);
   }

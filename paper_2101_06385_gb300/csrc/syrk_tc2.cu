@@ -271,6 +271,22 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 }  // namespace tc2
 
+// The dynamic shared-memory opt-in, once per kernel and device (not a stream
+// operation, and kept out of captured launch sequences).
+namespace {
+template <typename K>
+cudaError_t set_smem_once(K kernel, int bytes, int which) {
+  static int done_dev[2] = {-1, -1};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (done_dev[which] == dev) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done_dev[which] = dev;
+  return e;
+}
+}  // namespace
+
 size_t syrk_tc2_smem_bytes(bool split) {
   const int stages = split ? tc2::STAGES_SPLIT : tc2::STAGES_PLAIN;
   const int sb = split ? tc2::STAGE_SPLIT : tc2::STAGE_PLAIN;
@@ -294,11 +310,11 @@ cudaError_t launch_syrk_tc2(const SqArgs& a, const CUtensorMap* tm, bool split, 
   cfg.numAttrs = 1;
   cudaError_t e;
   if (split) {
-    e = cudaFuncSetAttribute(tc2::syrk_tc2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_smem_once(tc2::syrk_tc2_kernel<true>, (int)smem, 1);
     if (e != cudaSuccess) return e;
     e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<true>, tm[0], tm[1], tm[2], tm[3], a);
   } else {
-    e = cudaFuncSetAttribute(tc2::syrk_tc2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_smem_once(tc2::syrk_tc2_kernel<false>, (int)smem, 0);
     if (e != cudaSuccess) return e;
     e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<false>, tm[0], tm[1], tm[2], tm[3], a);
   }

@@ -77,3 +77,37 @@ def test_batched_reports_a_bad_instance(sp2):
     with pytest.raises(sp2.SP2Error) as e:
         sp2.density_matrix_batched(Hs, [50, 10])
     assert e.value.status == -3
+
+
+def test_graph_replay_matches_direct_launches(sp2):
+    """The batched launch sequence runs as a captured CUDA graph (captured on
+    the first call of a shape, replayed afterwards); both give the same bits
+    as enqueueing the launches directly (SP2_GRAPHS=0)."""
+    import os
+
+    sizes = [300, 64, 777, 128, 5]
+    hs = [si.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), seed=700 + i) for i, N in enumerate(sizes)]
+    Hs = [torch.from_numpy(h.h32()).cuda() for h in hs]
+    n_occ = [h.n_occ for h in hs]
+    D1, s1 = sp2.density_matrix_batched(Hs, n_occ)  # capture
+    D2, s2 = sp2.density_matrix_batched(Hs, n_occ)  # replay
+    # other data, same shape: replay of the same graph
+    hs_b = [si.gapped_hamiltonian(N, N // 2, (-1.0, -0.1), (0.1, 1.0), seed=800 + i) for i, N in enumerate(sizes)]
+    Db, sb = sp2.density_matrix_batched([torch.from_numpy(h.h32()).cuda() for h in hs_b], n_occ)
+    _check(hs_b, Db, sb)
+    sp2.finalize()
+    os.environ["SP2_GRAPHS"] = "0"
+    try:
+        sp2.init(0)
+        D3, s3 = sp2.density_matrix_batched(Hs, n_occ)
+    finally:
+        del os.environ["SP2_GRAPHS"]
+        sp2.finalize()
+        sp2.init(0)
+    _check(hs, D1, s1)
+    diffs = [(float((a - b).abs().max()), float((a - c).abs().max())) for a, b, c in zip(D1, D2, D3)]
+    print("graph replay / direct max-abs differences:", diffs, [s.iterations for s in s1], [s.iterations for s in s3])
+    for a, b, c in zip(D1, D2, D3):
+        assert torch.equal(a, b) and torch.equal(a, c)
+    assert [s.iterations for s in s1] == [s.iterations for s in s3]
+    assert all(len(s.layer_ms) == s.launches for s in s1)
