@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstddef>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -98,6 +99,9 @@ struct State {
   bool use_graphs = true;
   cudaGraphExec_t bgraph = nullptr;
   cudaStream_t cap_stream = nullptr;
+  // batched schedule: 0 tuned per batch signature, 1 single CTAs, 2 CTA pairs
+  int batched_sched = 0;
+  std::map<uint64_t, int> batched_choice;
   std::vector<uint64_t> bgraph_key;
 };
 
@@ -403,6 +407,8 @@ sp2_status sp2_init(const sp2_config* cfg) {
   {
     const char* kv = getenv("SP2_SQUARE_KERNEL");
     g.pair_kernel = !(kv && strcmp(kv, "single") == 0);
+    const char* bk = getenv("SP2_BATCHED_KERNEL");
+    g.batched_sched = (bk && strcmp(bk, "single") == 0) ? 1 : (bk && strcmp(bk, "pairs") == 0) ? 2 : 0;
     const char* gv = getenv("SP2_GRAPHS");
     g.use_graphs = !(gv && strcmp(gv, "0") == 0);
   }
@@ -781,28 +787,18 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
   return status_of(c, e);
 }
 
-sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const int* N_occ, int batch, double tol,
-                                      int max_iter, float* const* D_out, sp2_stats* stats) {
-  t_err.clear();
-  CKS(require_init());
-  if (!H || !N || !N_occ || !D_out || batch < 1 || batch > 4096 || !(tol >= 0.0) || !std::isfinite(tol) ||
-      max_iter < 1 || max_iter > SP2_MAX_LAYERS - 3) {
-    set_err("sp2_density_matrix_batched: invalid argument");
-    return SP2_ERR_INVALID_ARG;
-  }
-  int Nmax = 0;
-  for (int i = 0; i < batch; ++i) {
-    if (!H[i] || !D_out[i] || H[i] == D_out[i] || N[i] < 1 || N[i] > 4096 || N_occ[i] < 0 || N_occ[i] > N[i]) {
-      set_err("sp2_density_matrix_batched: invalid argument for instance %d", i);
-      return SP2_ERR_INVALID_ARG;
-    }
-    Nmax = std::max(Nmax, N[i]);
-  }
+namespace {
+
+// One batched solve on a fixed schedule (pairs: the CTA-pair squaring kernel
+// on super-tile pairs, else single CTAs on 128 x 256 tiles), enqueued on the
+// library stream; arguments checked by the caller.
+sp2_status batched_once(const float* const* H, const int* N, const int* N_occ, int B, int Nmax, double tol,
+                        int max_iter, float* const* D_out, bool pairs) {
   const int prec = g.precision;
   const bool tc = tc_precision(prec);
   const bool split = prec == SP2_PREC_SPLIT_FP16;
   cudaStream_t st = g.stream;
-  const int B = batch;
+  pairs = pairs && tc;
 
   // Tile list: instances by decreasing size (largest work first), the tiles
   // of one instance contiguous (its control step sums them in order).
@@ -815,7 +811,7 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   for (int b : order) {
     std::vector<uint32_t> one;
     int per = 0;
-    build_tiles(N[b], 1, tile, tc ? 1 : 0, one, per);
+    build_tiles(N[b], 1, tile, tc ? (pairs ? 2 : 1) : 0, one, per);
     toff[b] = (int)tiles.size();
     tcnt[b] = per;
     for (uint32_t t : one) tiles.push_back(t | ((uint32_t)b << 20));
@@ -903,8 +899,9 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   if (tc) {
     CKS(planes_for(split, 0, (size_t)slot_h * B * 2, &hi[0], &lo[0], &hp[0]));
     CKS(planes_for(split, 1, (size_t)slot_h * B * 2, &hi[1], &lo[1], &hp[1]));
-    CKS(tmaps4_for(split ? hp[0] : hi[0], lo[0], Nmax, B, ld_h, slot_h, m[0]));
-    CKS(tmaps4_for(split ? hp[1] : hi[1], lo[1], Nmax, B, ld_h, slot_h, m[1]));
+    const int boxb = pairs ? kTcBM : kTcBN;
+    CKS(tmaps4_for(split ? hp[0] : hi[0], lo[0], Nmax, B, ld_h, slot_h, m[0], boxb));
+    CKS(tmaps4_for(split ? hp[1] : hi[1], lo[1], Nmax, B, ld_h, slot_h, m[1], boxb));
     CKS(rnp_for(Nmax, B, A, rnp));
     A.Yin = (float*)Y[0];
     A.Yout = (float*)Y[0];
@@ -937,7 +934,7 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
                             nullptr, (double2*)part, (unsigned*)tick, g.shift, 1, B, igrid, st));
       CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
                         (double2*)part, (unsigned*)tick, rgrid, st));
-      const int grid = std::min(nt, g.num_sms);
+      const int grid = std::min(nt, g.num_sms) & (pairs ? ~1 : ~0);
       CK(cudaEventRecordWithFlags(g.lev[0], st, evf));
       for (int k = 0; k < max_iter + 2; ++k) {
         const int cur = k & 1;
@@ -945,7 +942,10 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
         A.lo_out = (__half*)lo[cur ^ 1];
         A.hp_out = (__half*)hp[cur ^ 1];
         rnp_step(A, rnp, k);
-        CK(launch_syrk_tc1(A, m[cur], split, grid, st));
+        if (pairs)
+          CK(launch_syrk_tc2(A, m[cur], split, grid, st));
+        else
+          CK(launch_syrk_tc1(A, m[cur], split, grid, st));
         CK(cudaEventRecordWithFlags(g.lsq[k], st, evf));
         CK(cudaEventRecordWithFlags(g.lev[k + 1], st, evf));
       }
@@ -975,7 +975,7 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   // it (sizes, grids, workspace addresses, stream) is unchanged; the per-call
   // records (control blocks, pointers, tile list) were uploaded above.
   if (g.use_graphs) {
-    const uint64_t key[] = {(uint64_t)B, (uint64_t)Nmax, (uint64_t)nt, (uint64_t)max_iter, (uint64_t)prec,
+    const uint64_t key[] = {(uint64_t)B, (uint64_t)Nmax, (uint64_t)nt, (uint64_t)max_iter, (uint64_t)prec, (uint64_t)pairs,
                             (uint64_t)g.shift, (uint64_t)g.lo_scale_exp, (uint64_t)igrid, (uint64_t)rgrid,
                             (uint64_t)ggrid, (uint64_t)g.num_sms, (uint64_t)(uintptr_t)st,
                             (uint64_t)(uintptr_t)hs, (uint64_t)(uintptr_t)ns, (uint64_t)(uintptr_t)ctl,
@@ -1013,7 +1013,76 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   } else {
     CKS(enqueue(st, false));
   }
+  return SP2_OK;
+}
+
+// Batch signature for the schedule cache: precision and the sorted sizes.
+uint64_t batch_signature(const int* N, int B) {
+  std::vector<int> v(N, N + B);
+  std::sort(v.begin(), v.end());
+  uint64_t h = 1469598103934665603ull ^ (uint64_t)g.precision;
+  for (int x : v) h = (h ^ (uint64_t)x) * 1099511628211ull;
+  return h ^ ((uint64_t)B << 40);
+}
+
+}  // namespace
+
+sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const int* N_occ, int batch, double tol,
+                                      int max_iter, float* const* D_out, sp2_stats* stats) {
+  t_err.clear();
+  CKS(require_init());
+  if (!H || !N || !N_occ || !D_out || batch < 1 || batch > 4096 || !(tol >= 0.0) || !std::isfinite(tol) ||
+      max_iter < 1 || max_iter > SP2_MAX_LAYERS - 3) {
+    set_err("sp2_density_matrix_batched: invalid argument");
+    return SP2_ERR_INVALID_ARG;
+  }
+  int Nmax = 0;
+  for (int i = 0; i < batch; ++i) {
+    if (!H[i] || !D_out[i] || H[i] == D_out[i] || N[i] < 1 || N[i] > 4096 || N_occ[i] < 0 || N_occ[i] > N[i]) {
+      set_err("sp2_density_matrix_batched: invalid argument for instance %d", i);
+      return SP2_ERR_INVALID_ARG;
+    }
+    Nmax = std::max(Nmax, N[i]);
+  }
+  const int prec = g.precision;
+  const bool tc = tc_precision(prec);
+  cudaStream_t st = g.stream;
+  const int B = batch;
+
+  // schedule: fixed (SP2_BATCHED_KERNEL=single|pairs) or tuned once per batch
+  // signature by timing each candidate on the call itself (every candidate
+  // run is a complete solve, so the last one leaves valid results)
+  bool pairs = g.batched_sched == 2;
+  bool solved = false;
+  if (tc && g.batched_sched == 0) {
+    const uint64_t sig = batch_signature(N, B);
+    auto it = g.batched_choice.find(sig);
+    if (it != g.batched_choice.end()) {
+      pairs = it->second != 0;
+    } else {
+      float best = 0.f;
+      int pick = 0;
+      for (int cand = 0; cand < 2; ++cand) {
+        CKS(batched_once(H, N, N_occ, B, Nmax, tol, max_iter, D_out, cand != 0));
+        CK(cudaEventSynchronize(g.ev1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, g.ev0, g.ev1));
+        if (cand == 0 || ms < best) {
+          best = ms;
+          pick = cand;
+        }
+      }
+      g.batched_choice[sig] = pick;
+      pairs = pick != 0;
+      // the last candidate's run (pairs) is the result when it won
+      solved = pick == 1;
+    }
+  }
+  if (!solved) CKS(batched_once(H, N, N_occ, B, Nmax, tol, max_iter, D_out, pairs));
+
   if (!stats) return SP2_OK;
+  void* ctl = g.buf[B_CTL].p;
+  void* err = g.buf[B_ERR].p;
 
   void* hb;
   CKS(staging((size_t)B * sizeof(Ctl) + 16, &hb));

@@ -111,3 +111,33 @@ def test_graph_replay_matches_direct_launches(sp2):
         assert torch.equal(a, b) and torch.equal(a, c)
     assert [s.iterations for s in s1] == [s.iterations for s in s3]
     assert all(len(s.layer_ms) == s.launches for s in s1)
+
+
+@pytest.mark.parametrize("sizes", [[64, 1000, 257, 130, 1], [512] * 6])
+def test_schedules_agree(sp2, sizes):
+    """Single CTAs on 128 x 256 tiles and CTA pairs on 256 x 256 super tiles
+    (the two schedules the batched autotuner chooses from) give the same bits:
+    each tile accumulates its products in the same order either way."""
+    import os
+
+    hs = [si.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), seed=900 + i) for i, N in enumerate(sizes)]
+    Hs = [torch.from_numpy(h.h32()).cuda() for h in hs]
+    n_occ = [h.n_occ for h in hs]
+    out = {}
+    try:
+        for sched in ("single", "pairs"):
+            sp2.finalize()
+            os.environ["SP2_BATCHED_KERNEL"] = sched
+            sp2.init(0)
+            out[sched] = sp2.density_matrix_batched(Hs, n_occ)
+    finally:
+        os.environ.pop("SP2_BATCHED_KERNEL", None)
+        sp2.finalize()
+        sp2.init(0)
+    _check(hs, *out["pairs"])
+    for a, b in zip(out["single"][0], out["pairs"][0]):
+        assert torch.equal(a, b)
+    # the tuned default picks one of the two and matches both
+    Dt, _ = sp2.density_matrix_batched(Hs, n_occ)
+    for a, b in zip(out["single"][0], Dt):
+        assert torch.equal(a, b)
