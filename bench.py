@@ -165,6 +165,19 @@ def _traffic_from_profile(n):
     return float(t.group(1)) if kernel_source_hash() == m.group(1) else None
 
 
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":")[0].strip().lower()
+            if k in ("model name", "cpu model", "hardware"):
+                return line.split(":", 1)[1].strip()
+        import platform
+
+        return platform.processor() or platform.machine()
+    except OSError:
+        return None
+
+
 def _cpu_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -376,6 +389,16 @@ def run_ours(args):
     max_abs = float(np.max(np.abs(diff)))
     rel_frob = float(np.sqrt(np.mean(diff ** 2) / max(np.mean(ref ** 2), 1e-300)))
     trace_err = abs(float(np.trace(Dh.astype(np.float64))) - n_occ)
+    # idempotency and commutator with H on 256 sampled rows (FP32 products on
+    # the device, outside the timed region)
+    with torch.no_grad():
+        rr = torch.from_numpy(np.sort(rng.choice(N, 256, replace=False))).to(dev)
+        prev_tf32 = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        Dr, Hr = D.index_select(0, rr), H.index_select(0, rr)
+        idem = float((Dr @ D - Dr).abs().max())
+        comm = float((Dr @ H - Hr @ D).abs().max())
+        torch.backends.cuda.matmul.allow_tf32 = prev_tf32
 
     # FP32 (FFMA) comparator on the same input
     fp32 = None
@@ -420,8 +443,21 @@ def run_ours(args):
         t0 = time.perf_counter()
         oracle.sp2_layer_sample(S0, rows)
         dt = time.perf_counter() - t0
+        # the same oracle layer on one core, on a smaller block of rows
+        one_core = None
+        try:
+            from threadpoolctl import threadpool_limits
+
+            r1 = 256
+            with threadpool_limits(limits=1):
+                t1 = time.perf_counter()
+                oracle.sp2_layer_sample(S0, r1)
+                d1 = time.perf_counter() - t1
+            one_core = {"value": 2.0 * r1 * N * N / d1 / 1e12, "unit": "TFLOP/s", "rows": r1, "seconds": d1}
+        except ImportError:
+            pass
         cpu = {"value": 2.0 * rows * N * N / dt / 1e12, "unit": "TFLOP/s", "cores": _cpu_threads(),
-               "kind": "oracle",
+               "kind": "oracle", "cpu_model": _cpu_model(), "one_core": one_core,
                "sample": f"one FP64 SP2 layer restricted to {rows} of {N} rows (S[:rows] @ S + update + trace), "
                          f"{dt:.1f} s; full solve would be ~{layers} layers x {N // rows} blocks"}
         del S0, H64
@@ -449,6 +485,8 @@ def run_ours(args):
                    "paper_convention_tflops": st.iterations * 4.0 * N ** 3 / (sum(
                        st.layer_ms[: st.iterations]) * 1e-3) / 1e12},
         "accuracy": {"max_abs_err_sampled": max_abs, "rel_frob_sampled": rel_frob, "trace_err": trace_err,
+                     "idempotency_max_abs_sampled_rows": idem, "commutator_max_abs_sampled_rows": comm,
+                     "idemp_err_last_layer": st.idemp_err,
                      "samples": int(len(diff)), "tolerance_max_abs": 5e-5, "tolerance_trace": 1e-4},
         "fp32_path": fp32,
         "e2e": {"value": e2e_value, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
