@@ -27,6 +27,10 @@ split_fp16                     brute-force nearest-FP16 search on small inputs;
 split_square                   exact FP64 product of FP16-exact operands
 network_forward                scalar polynomial composition on eigenvalues
 network_adjoint                central finite differences of network_forward
+accelerated_layer              fixed points and fold of each layer polynomial;
+                               bounds enclose the true eigenvalue images
+sp2_accelerated                closed form Q_occ Q_occ^T; layer-count reduction
+                               against sp2 (Fig. AccConv trend)
 =============================  =================================================
 
 Readings of points the paper leaves open (same list as the design notes):
@@ -40,6 +44,18 @@ C7  f_final is applied to the last computed S_n and its branch is read from
     sigma_{n-2}; when n < 3 (sigma_{n-2} undefined or 0) the x^2-first order
     (2S^2 - S^4) is used.
 C11 optional ``tol``: stop as soon as IdErr_n <= tol.
+C19 accelerated SP2 (Sec. "Accelerated Deep-NN SP2"; its formulas are in a
+    supplement that is not available): with the unoccupied eigenvalues of the
+    scaled iterate in [0, l] and the occupied ones in [h, 1], a layer squares
+    the side farther from its fixed point after a shift-and-rescale that
+    folds that side onto itself: if 1 - h <= l, x -> ((x - l/2)/(1 - l/2))^2
+    (0 and l land on the same value), else the mirror image
+    x -> 1 - ((1 - x - b)/(1 - b))^2 with b = (1 - h)/2.  Both fix 0 and 1
+    and keep the two sets apart; the bounds follow exactly.
+C20 the accelerated scheme stops once max(l, 1 - h) <= tol (a bound on the
+    eigenvalue distance of the iterate from 0 and 1); no f_final follows.
+C21 HOMO/LUMO energies are caller estimates; they are safe when the gap they
+    span lies inside the true one (homo >= true HOMO, lumo <= true LUMO).
 """
 from __future__ import annotations
 
@@ -50,6 +66,9 @@ from typing import List, Optional, Sequence, Tuple
 import numpy as np
 
 __all__ = [
+    "accelerated_layer",
+    "sp2_accelerated",
+    "AccelResult",
     "gershgorin_bounds",
     "input_layer",
     "sigma_choice",
@@ -191,6 +210,86 @@ def sp2(
     D = f_final(S, s_nm2) if refine else S.copy()
     return SP2Result(D=D, S_last=S, sigmas=sig_hist[1:], iderr=err_hist[1:], traces=traces,
                      n_layers=n, converged_by=how, e_min=e_min, e_max=e_max)
+
+
+def accelerated_layer(l: float, h: float) -> Tuple[float, float, float, int, float, float]:
+    """One layer of the accelerated scheme (Sec. "Accelerated Deep-NN SP2",
+    reading C19) on the spectral bounds of the scaled iterate: unoccupied
+    eigenvalues in [0, l], occupied in [h, 1], 0 <= l < h <= 1.
+
+    Returns (a, b, c, sigma, l', h') with the layer X' = a X^2 + b X + c I
+    (the generalised layer of Eq. 16) and the bounds of X'.
+
+    sigma = +1 (1 - h <= l): shift by s = l/2 and rescale so that 1 stays
+    fixed, then square:  p(x) = ((x - s)/(1 - s))^2.  On [0, l] p folds
+    around s, with p(0) = p(l) = s^2/(1 - s)^2 as its maximum; on [h, 1] it
+    is increasing, so h' = p(h).
+    sigma = -1: the mirror image under x -> 1 - x with t = (1 - h)/2,
+    q(x) = 1 - ((1 - x - t)/(1 - t))^2 = 2x/(1 - t) - x^2/(1 - t)^2.
+    """
+    if not (0.0 <= l < h <= 1.0):
+        raise ValueError("need 0 <= l < h <= 1")
+    if 1.0 - h <= l:
+        s = 0.5 * l
+        d = 1.0 - s
+        a, b, c = 1.0 / (d * d), -2.0 * s / (d * d), s * s / (d * d)
+        l2 = (s / d) ** 2
+        h2 = ((h - s) / d) ** 2
+        return a, b, c, 1, l2, h2
+    t = 0.5 * (1.0 - h)
+    d = 1.0 - t
+    a, b, c = -1.0 / (d * d), 2.0 / d, 0.0
+    h2 = 1.0 - (t / d) ** 2
+    l2 = 1.0 - ((1.0 - l - t) / d) ** 2
+    return a, b, c, -1, l2, h2
+
+
+@dataclasses.dataclass
+class AccelResult:
+    D: np.ndarray
+    n_layers: int
+    sigmas: List[int]
+    coefficients: List[Tuple[float, float, float]]
+    bounds: List[Tuple[float, float]]   # (l_n, h_n) after layer n; entry 0 = input layer
+    e_min: float
+    e_max: float
+
+
+def sp2_accelerated(H: np.ndarray, n_occ: int, homo: float, lumo: float, tol: float = 1e-10,
+                    max_iter: int = 100, bounds: Optional[Tuple[float, float]] = None) -> AccelResult:
+    """Accelerated Deep-NN SP2 in FP64 (Sec. "Accelerated Deep-NN SP2",
+    readings C19-C21).
+
+    S_0 is the input layer of Alg. 1.  The caller's HOMO/LUMO energies give
+    the initial bounds in the scaled variable x = (e_max - eps)/(e_max - e_min):
+    unoccupied x <= l_0 = (e_max - lumo)/(e_max - e_min), occupied
+    x >= h_0 = (e_max - homo)/(e_max - e_min).  Each layer applies
+    ``accelerated_layer``'s polynomial to S and updates the bounds; the loop
+    stops once max(l, 1 - h) <= tol or after max_iter layers.  n_occ is not
+    used by the iteration (the bounds decide); it is kept for the caller's
+    trace check.
+    """
+    H = np.asarray(H, dtype=np.float64)
+    N = H.shape[0]
+    e_min, e_max = gershgorin_bounds(H) if bounds is None else bounds
+    S = input_layer(H, e_min, e_max)
+    w = e_max - e_min
+    l = min(max((e_max - lumo) / w, 0.0), 1.0)
+    h = min(max((e_max - homo) / w, 0.0), 1.0)
+    if not l < h:
+        raise ValueError("HOMO/LUMO estimates leave no gap inside the spectral bounds")
+    sig: List[int] = []
+    coef: List[Tuple[float, float, float]] = []
+    hist = [(l, h)]
+    n = 0
+    while n < max_iter and max(l, 1.0 - h) > tol:
+        a, b, c, s_, l, h = accelerated_layer(l, h)
+        S = a * (S @ S) + b * S + c * np.eye(N)
+        n += 1
+        sig.append(s_)
+        coef.append((a, b, c))
+        hist.append((l, h))
+    return AccelResult(D=S, n_layers=n, sigmas=sig, coefficients=coef, bounds=hist, e_min=e_min, e_max=e_max)
 
 
 def f_final(S: np.ndarray, sigma_nm2: int) -> np.ndarray:
