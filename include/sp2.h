@@ -52,7 +52,9 @@ typedef enum {
   SP2_ERR_CUDA = -5,
   SP2_ERR_OOM = -6,
   SP2_ERR_DEVICE_TIMEOUT = -7,      /* a bounded device wait ran out */
-  SP2_ERR_UNSUPPORTED = -8
+  SP2_ERR_UNSUPPORTED = -8,
+  SP2_ERR_BAD_ESTIMATE = -9         /* accelerated solve: the HOMO/LUMO estimates were not safe
+                                       (Tr D differs from N_occ by more than 1/2) */
 } sp2_status;
 
 typedef enum {
@@ -66,7 +68,8 @@ typedef enum {
   SP2_STOP_TOL = 1,      /* IdErr_n <= tol */
   SP2_STOP_IDERR = 2,    /* IdErr_n <= 0 (Alg. 1) */
   SP2_STOP_RULE45 = 3,   /* IdErr_n > 4.5 IdErr_{n-2}^2 after a sign change (Alg. 1, appendix) */
-  SP2_STOP_MAXITER = 4   /* n == max_iter: returns SP2_NOT_CONVERGED */
+  SP2_STOP_MAXITER = 4,  /* n == max_iter: returns SP2_NOT_CONVERGED */
+  SP2_STOP_BOUNDS = 5    /* accelerated solve: eigenvalue bounds within tol of 0 and 1 */
 } sp2_stop_reason;
 
 typedef struct {
@@ -133,6 +136,35 @@ const char* sp2_last_error(void);
  */
 sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int max_iter,
                               float* D_out, sp2_stats* stats);
+
+/*
+ * Accelerated Deep-NN SP2 (Sec. "Accelerated Deep-NN SP2"): each layer is a
+ * generalised layer X' = a X^2 + b X + c I chosen from bounds on the scaled
+ * spectrum instead of the trace rule.  With the unoccupied eigenvalues of
+ * the scaled iterate in [0, l] and the occupied ones in [h, 1]: if
+ * 1 - h <= l the layer is x -> ((x - l/2)/(1 - l/2))^2, else
+ * x -> 1 - ((1 - x - t)/(1 - t))^2 with t = (1 - h)/2; both fix 0 and 1,
+ * keep the two sets apart, and give the next bounds in closed form.  The
+ * solve stops once max(l, 1 - h) <= tol; D_out is the last layer (no Eq. 15
+ * refinement).
+ *
+ *   homo, lumo  estimates of the highest occupied and lowest unoccupied
+ *               eigenvalues of H (e.g. from a previous step of a dynamics
+ *               run).  Safe when homo >= true HOMO and lumo <= true LUMO
+ *               (a narrower gap); homo < lumo required.  The initial bounds
+ *               are l = (e_max - lumo)/(e_max - e_min), h = (e_max - homo)/
+ *               (e_max - e_min) with the Gershgorin e_min, e_max, clamped to
+ *               [0, 1]; the device reports SP2_ERR_INVALID_ARG when l >= h.
+ *   tol         bound tolerance, 0 selects 1e-9.
+ *   max_iter    layer limit as for sp2_density_matrix (SP2_NOT_CONVERGED
+ *               when it is reached first).
+ *   other arguments and ownership as for sp2_density_matrix.
+ * Errors: as sp2_density_matrix, plus INVALID_ARG for non-finite or
+ * gapless estimates and BAD_ESTIMATE when Tr D misses N_occ by more than
+ * 1/2 (D_out then holds the wrong projection).
+ */
+sp2_status sp2_density_matrix_accelerated(const float* H, int N, int N_occ, double homo, double lumo, double tol,
+                                          int max_iter, float* D_out, sp2_stats* stats);
 
 /*
  * Many independent SP2 problems of uneven size in grouped launches (the

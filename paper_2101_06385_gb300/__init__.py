@@ -51,8 +51,9 @@ _STATUS = {
     -6: "SP2_ERR_OOM",
     -7: "SP2_ERR_DEVICE_TIMEOUT",
     -8: "SP2_ERR_UNSUPPORTED",
+    -9: "SP2_ERR_BAD_ESTIMATE",
 }
-_STOP = {0: "none", 1: "tol", 2: "iderr<=0", 3: "4.5-rule", 4: "max_iter"}
+_STOP = {0: "none", 1: "tol", 2: "iderr<=0", 3: "4.5-rule", 4: "max_iter", 5: "bounds"}
 
 
 class SP2Error(RuntimeError):
@@ -146,6 +147,7 @@ def _load():
         "sp2_set_precision": (_I, [_I]),
         "sp2_last_error": (ctypes.c_char_p, []),
         "sp2_density_matrix": (_I, [_P, _I, _I, _D, _I, _P, ctypes.POINTER(_Stats)]),
+        "sp2_density_matrix_accelerated": (_I, [_P, _I, _I, _D, _D, _D, _I, _P, ctypes.POINTER(_Stats)]),
         "sp2_density_matrix_batched": (_I, [_P, _P, _P, _I, _D, _I, _P, _P]),
         "sp2_network_forward": (_I, [_P, _I, _I, _I, _P, _I, _P, _P, _P]),
         "sp2_network_backward": (_I, [_P, _I, _I, _I, _P, _I, _P, _P, _P, _P]),
@@ -280,6 +282,30 @@ def density_matrix(H: torch.Tensor, n_occ: int, tol: float = 0.0, max_iter: int 
     with _precision(precision):
         status = lib.sp2_density_matrix(H.data_ptr(), N, int(n_occ), float(tol), int(max_iter), D.data_ptr(),
                                         ctypes.byref(st) if sync else None)
+    _check(status, allow=(0, 1))
+    return D, (_stats(st, status) if sync else None)
+
+
+def density_matrix_accelerated(H: torch.Tensor, n_occ: int, homo: float, lumo: float, tol: float = 0.0,
+                               max_iter: int = 100, out: Optional[torch.Tensor] = None,
+                               precision: Optional[str] = None, sync: bool = True):
+    """D = theta(mu I - H) by the accelerated Deep-NN SP2 layers, given
+    estimates of the HOMO and LUMO eigenvalues of H (a narrower gap than the
+    true one is safe).  ``tol`` bounds the eigenvalue distance from 0 and 1
+    (0 selects 1e-9).  Returns (D, stats)."""
+    _dev_f32(H, "H")
+    if H.dim() != 2 or H.shape[0] != H.shape[1]:
+        raise ValueError("H must be square")
+    _ensure_init(H)
+    lib = _load()
+    N = H.shape[0]
+    D = out if out is not None else torch.empty_like(H)
+    _dev_f32(D, "out")
+    st = _Stats()
+    with _precision(precision):
+        status = lib.sp2_density_matrix_accelerated(H.data_ptr(), N, int(n_occ), float(homo), float(lumo),
+                                                    float(tol), int(max_iter), D.data_ptr(),
+                                                    ctypes.byref(st) if sync else None)
     _check(status, allow=(0, 1))
     return D, (_stats(st, status) if sync else None)
 

@@ -327,7 +327,7 @@ void fill_stats(const Ctl& c, sp2_stats* s, double ms, int precision) {
   s->time_ms = ms;
   const double N = (double)c.N;
   const double per = (precision == SP2_PREC_SPLIT_FP16 ? 3.0 : 1.0) * N * N * N;
-  s->flops_alg = (c.phase == PHASE_DONE ? (c.n + 2) : c.n) * per;
+  s->flops_alg = (c.phase == PHASE_DONE && !c.accel ? (c.n + 2) : c.n) * per;
   for (int k = 0; k < kMaxL; ++k) {
     s->sigma[k] = (k + 1 <= c.n) ? (int8_t)c.sigma[k + 1] : 0;
     s->iderr[k] = (k + 1 <= c.n) ? c.iderr[k + 1] : 0.0;
@@ -340,8 +340,9 @@ sp2_status status_of(const Ctl& c, int dev_err) {
     return SP2_ERR_DEVICE_TIMEOUT;
   }
   if (c.status < 0) {
-    set_err(c.status == SP2_ERR_NONFINITE ? "non-finite spectral bounds (NaN or Inf in H)"
-                                          : "degenerate spectrum: e_max - e_min <= 0 with 0 < N_occ < N");
+    set_err(c.status == SP2_ERR_NONFINITE      ? "non-finite spectral bounds (NaN or Inf in H)"
+            : c.status == SP2_ERR_INVALID_ARG  ? "HOMO/LUMO estimates leave no gap inside the spectral bounds"
+                                               : "degenerate spectrum: e_max - e_min <= 0 with 0 < N_occ < N");
     return (sp2_status)c.status;
   }
   if (c.phase != PHASE_DONE) {
@@ -623,15 +624,12 @@ sp2_status sp2_layer(const float* X, int B, int N, float a, float b, float c, fl
   return SP2_OK;
 }
 
-sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int max_iter, float* D_out,
-                              sp2_stats* stats) {
-  t_err.clear();
-  CKS(require_init());
-  if (!H || !D_out || H == D_out || N < 1 || N > 65536 || N_occ < 0 || N_occ > N || !(tol >= 0.0) ||
-      !std::isfinite(tol) || max_iter < 1 || max_iter > SP2_MAX_LAYERS - 3) {
-    set_err("sp2_density_matrix: invalid argument");
-    return SP2_ERR_INVALID_ARG;
-  }
+namespace {
+
+// The single-matrix solve; accel selects the accelerated layers (bounds from
+// the HOMO/LUMO estimates) instead of the trace rule with refinement.
+sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int max_iter, float* D_out,
+                               sp2_stats* stats, bool accel, double homo, double lumo) {
   const int prec = g.precision;
   const bool tc = tc_precision(prec);
   const bool split = prec == SP2_PREC_SPLIT_FP16;
@@ -658,6 +656,15 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
   CKS(staging(sizeof(Ctl) + 64, &h));
   Ctl* hc = (Ctl*)h;
   init_ctl(hc, N, N_occ, tol, max_iter);
+  if (accel) {
+    hc->accel = 1;
+    hc->acc_homo = homo;
+    hc->acc_lumo = lumo;
+    hc->tol = tol > 0.0 ? tol : 1e-9;
+  }
+  // launches enqueued: the loop's layers plus the two of Eq. 15 (the
+  // accelerated solve has no refinement layers)
+  const int nlaunch = accel ? max_iter : max_iter + 2;
   int* hn = (int*)(hc + 1);
   hn[0] = N;
   const float** hh = (const float**)(hn + 2);
@@ -723,7 +730,7 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
     CKS(rnp_for(N, 1, A, rnp));
     A.fused_ctl = 1;
     CK(cudaEventRecord(g.lev[0], st));
-    for (int k = 0; k < max_iter + 2; ++k) {
+    for (int k = 0; k < nlaunch; ++k) {
       const int cur = k & 1;
       A.hi_out = (__half*)hi[cur ^ 1];
       A.lo_out = (__half*)lo[cur ^ 1];
@@ -749,7 +756,7 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
     A.ld_y = ld_y;
     A.slot_y = slot_y;
     CK(cudaEventRecord(g.lev[0], st));
-    for (int k = 0; k < max_iter + 2; ++k) {
+    for (int k = 0; k < nlaunch; ++k) {
       const int cur = k & 1;
       A.Yin = (float*)Y[cur];
       A.Yout = (float*)Y[cur ^ 1];
@@ -773,18 +780,51 @@ sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int 
   const Ctl& c = *(const Ctl*)hb;
   const int e = *(const int*)((char*)hb + sizeof(Ctl));
   fill_stats(c, stats, ms, prec);
-  stats->launches = max_iter + 2;
+  stats->launches = nlaunch;
   float pm = 0.f;
   CK(cudaEventElapsedTime(&pm, g.ev0, g.lev[0]));
   stats->prologue_ms = pm;
-  for (int k = 0; k < max_iter + 2; ++k) {
+  for (int k = 0; k < nlaunch; ++k) {
     float lm = 0.f, sm = 0.f;
     CK(cudaEventElapsedTime(&lm, g.lev[k], g.lev[k + 1]));
     CK(cudaEventElapsedTime(&sm, g.lev[k], g.lsq[k]));
     stats->layer_ms[k] = lm;
     stats->square_ms[k] = sm;
   }
-  return status_of(c, e);
+  const sp2_status rs = status_of(c, e);
+  if (accel && rs >= 0 && std::fabs(c.trace_final - (double)N_occ) > 0.5) {
+    set_err("accelerated solve: Tr D = %.3f but N_occ = %d; the HOMO/LUMO estimates do not bracket the gap",
+            c.trace_final, N_occ);
+    return SP2_ERR_BAD_ESTIMATE;
+  }
+  return rs;
+}
+
+}  // namespace
+
+sp2_status sp2_density_matrix(const float* H, int N, int N_occ, double tol, int max_iter, float* D_out,
+                              sp2_stats* stats) {
+  t_err.clear();
+  CKS(require_init());
+  if (!H || !D_out || H == D_out || N < 1 || N > 65536 || N_occ < 0 || N_occ > N || !(tol >= 0.0) ||
+      !std::isfinite(tol) || max_iter < 1 || max_iter > SP2_MAX_LAYERS - 3) {
+    set_err("sp2_density_matrix: invalid argument");
+    return SP2_ERR_INVALID_ARG;
+  }
+  return density_matrix_impl(H, N, N_occ, tol, max_iter, D_out, stats, false, 0.0, 0.0);
+}
+
+sp2_status sp2_density_matrix_accelerated(const float* H, int N, int N_occ, double homo, double lumo, double tol,
+                                          int max_iter, float* D_out, sp2_stats* stats) {
+  t_err.clear();
+  CKS(require_init());
+  if (!H || !D_out || H == D_out || N < 1 || N > 65536 || N_occ < 0 || N_occ > N || !(tol >= 0.0) ||
+      !std::isfinite(tol) || max_iter < 1 || max_iter > SP2_MAX_LAYERS - 3 || !std::isfinite(homo) ||
+      !std::isfinite(lumo) || !(homo < lumo)) {
+    set_err("sp2_density_matrix_accelerated: invalid argument");
+    return SP2_ERR_INVALID_ARG;
+  }
+  return density_matrix_impl(H, N, N_occ, tol, max_iter, D_out, stats, true, homo, lumo);
 }
 
 namespace {

@@ -66,6 +66,10 @@ struct Ctl {
   LayerParams next;           // parameters of the next squaring launch
   int sigma[kMaxL + 1];       // sigma[k] = sigma_k, sigma[0] = 0
   double iderr[kMaxL + 1];    // iderr[k] = IdErr_k
+  // accelerated solve (Sec. "Accelerated Deep-NN SP2")
+  int accel, pad2;
+  double acc_homo, acc_lumo;  // caller's HOMO / LUMO energy estimates
+  double acc_l, acc_h;        // unoccupied eigenvalues of the scaled iterate in [0, l], occupied in [h, 1]
 };
 
 // ---------------------------------------------------------------- helpers
@@ -118,10 +122,108 @@ __device__ inline void set_branch(Ctl* c, int sigma, bool final_layer) {
 // the Y just stored.  Decides sigma_{n+1}, IdErr_{n+1} and the stop rules
 // (IdErr <= tol, IdErr <= 0, the 4.5 rule after a sign change, max_iter), or
 // moves on to the two refinement layers of Eq. 15.
+// Generalised layer S' = a S^2 + b S + c I on the stored S = alpha I + Y:
+// S' = (a alpha^2 + b alpha + c) I + (2 a alpha + b) Y + a Y^2.
+__device__ inline void set_poly(Ctl* c, double a, double b, double cp, bool final_layer) {
+  const double al = c->alpha;
+  double an = a * al * al + b * al + cp;
+  const double ca = 2.0 * a * al + b, cb = a;
+  double cc = 0.0;
+  if (c->recentered) {
+    cc = an - 0.5;
+    an = 0.5;
+  } else if (!c->shift) {
+    cc = an;
+    an = 0.0;
+  }
+  c->alpha_next = an;
+  LayerParams p;
+  p.ca = (float)ca;
+  p.cb = (float)cb;
+  p.ca_d = ca;
+  p.cb_d = cb;
+  p.cc_d = cc;
+  p.alpha_out = final_layer ? an : 0.0;
+  p.active = 1;
+  p.out_mode = final_layer ? OUT_D : OUT_Y;
+  c->next = p;
+}
+
+// Layer of the accelerated scheme on bounds (l, h): shift and rescale so the
+// side farther from its fixed point folds onto itself, then square.
+//   1 - h <= l: p(x) = ((x - s)/(1 - s))^2, s = l/2   (0 and l meet at p = (s/(1-s))^2)
+//   otherwise:  q(x) = 1 - ((1 - x - t)/(1 - t))^2, t = (1 - h)/2
+__device__ inline int accel_layer(double& l, double& h, double& a, double& b, double& cp) {
+  if (1.0 - h <= l) {
+    const double s = 0.5 * l, d = 1.0 - s;
+    a = 1.0 / (d * d);
+    b = -2.0 * s / (d * d);
+    cp = s * s / (d * d);
+    const double hs = (h - s) / d;
+    l = (s / d) * (s / d);
+    h = hs * hs;
+    return 1;
+  }
+  const double t = 0.5 * (1.0 - h), d = 1.0 - t;
+  a = -1.0 / (d * d);
+  b = 2.0 / d;
+  cp = 0.0;
+  const double lt = (1.0 - l - t) / d;
+  h = 1.0 - (t / d) * (t / d);
+  l = 1.0 - lt * lt;
+  return -1;
+}
+
+// Control step of the accelerated solve: the layers follow the bounds alone;
+// IdErr is recorded for the statistics and the re-centring of the shift.
+__device__ inline void accel_control_step(Ctl* c, double trY, double sqY) {
+  const double N = (double)c->N;
+  if (c->phase == PHASE_LOOP) {
+    const int n1 = c->n + 1;
+    const double a = c->alpha;
+    const double err = N * a * (1.0 - a) + (1.0 - 2.0 * a) * trY - sqY;
+    if (c->n == 0) {
+      const double w = c->e_max - c->e_min;
+      c->acc_l = fmin(fmax((c->e_max - c->acc_lumo) / w, 0.0), 1.0);
+      c->acc_h = fmin(fmax((c->e_max - c->acc_homo) / w, 0.0), 1.0);
+      if (!(c->acc_l < c->acc_h)) {
+        c->status = SP2_ERR_INVALID_ARG;
+        c->phase = PHASE_ERROR;
+        c->next.active = 0;
+        return;
+      }
+    }
+    c->iderr[n1] = err;
+    if (c->shift && !c->recentered && err <= kRecenterFrac * N) c->recentered = 1;
+    double l = c->acc_l, h = c->acc_h, pa, pb, pc;
+    const int s = accel_layer(l, h, pa, pb, pc);
+    c->acc_l = l;
+    c->acc_h = h;
+    c->sigma[n1] = s;
+    c->n = n1;
+    const bool done = fmax(l, 1.0 - h) <= c->tol;
+    const bool final_layer = done || n1 >= c->max_iter;
+    if (final_layer) {
+      c->converged_by = done ? SP2_STOP_BOUNDS : SP2_STOP_MAXITER;
+      c->phase = PHASE_REFINE_B;  // the next step (after the OUT_D launch) finishes
+    }
+    set_poly(c, pa, pb, pc, final_layer);
+  } else if (c->phase == PHASE_REFINE_B) {
+    c->trace_final = N * c->alpha + trY;
+    c->phase = PHASE_DONE;
+    c->next.active = 0;
+    if (c->status == SP2_OK && c->converged_by == SP2_STOP_MAXITER) c->status = SP2_NOT_CONVERGED;
+  }
+}
+
 __device__ inline void control_step(Ctl* c, double trY, double sqY) {
   c->trY = trY;
   c->sqY = sqY;
   c->alpha = c->alpha_next;
+  if (c->accel) {
+    accel_control_step(c, trY, sqY);
+    return;
+  }
   const double N = (double)c->N;
   if (c->phase == PHASE_LOOP) {
     if (c->stop_pending) {
