@@ -83,6 +83,25 @@ def _peaks():
     return FALLBACK_PEAKS, "fallback"
 
 
+def replica_time_max(ms, dev, ws):
+    """Whole-job time of N independent replicas: the slowest rank's time
+    (all-reduce MAX over the process group; identity on one rank)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, ms, ws):
+    """Aggregate rate of ws replicas that each processed units_per_rank in the
+    whole-job time ms (weak scaling: per-rank work fixed)."""
+    return units_per_rank * ws / (ms * 1e-3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -354,15 +373,11 @@ def run_ours(args):
     e1.record()
     barrier()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replica_time_max(e0.elapsed_time(e1) / args.steps, dev, ws)
     st = stats[-1]
     layers = st.iterations + 2
     flops_eff = layers * 2.0 * N ** 3
-    value = flops_eff * ws / (ms * 1e-3) / 1e12
+    value = replica_throughput(flops_eff, ms, ws) / 1e12
 
     # squaring kernel: active launches of the timed steps
     act = [x for s in stats for x in s.square_ms[: s.iterations + 2]]
@@ -432,8 +447,8 @@ def run_ours(args):
         e2e_layers += se.iterations + 2
     s1.record()
     barrier()
-    e2e_ms = s0.elapsed_time(s1) / args.e2e_steps
-    e2e_value = (e2e_layers / args.e2e_steps) * 2.0 * N ** 3 * ws / (e2e_ms * 1e-3) / 1e12
+    e2e_ms = replica_time_max(s0.elapsed_time(s1) / args.e2e_steps, dev, ws)
+    e2e_value = replica_throughput((e2e_layers / args.e2e_steps) * 2.0 * N ** 3, e2e_ms, ws) / 1e12
 
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
