@@ -238,21 +238,6 @@ bool make_tmap_f16(CUtensorMap* out, const void* base, int cols, int rows, int b
 
 namespace {
 
-// Tensor maps {hiA, loA, hiB, loB} over split buffers (hi, lo) of B
-// instances with N x N used entries, row stride ld_h, slot stride slot_h.
-sp2_status tmaps_for(const void* hi, const void* lo, int N, int B, long long ld_h, long long slot_h, CUtensorMap* m) {
-  const void* lo_ = lo ? lo : hi;
-  bool ok = make_tmap_f16(&m[0], hi, N, N, B, ld_h, slot_h, 64, kTcBM) &&
-            make_tmap_f16(&m[1], lo_, N, N, B, ld_h, slot_h, 64, kTcBM) &&
-            make_tmap_f16(&m[2], hi, N, N, B, ld_h, slot_h, 64, kTcBN) &&
-            make_tmap_f16(&m[3], lo_, N, N, B, ld_h, slot_h, 64, kTcBN);
-  if (!ok) {
-    set_err("cuTensorMapEncodeTiled failed (N=%d, ld=%lld)", N, ld_h);
-    return SP2_ERR_CUDA;
-  }
-  return SP2_OK;
-}
-
 // Tensor maps {p0(A box), p1(A box), p0(B box), p1(B box)} for the
 // single-accumulator squaring kernels: p0 = hp = 2^s hi and p1 = lo' for the
 // split product, p0 = hi (p1 unused, null) for plain FP16.
@@ -1453,11 +1438,12 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
   CK(cudaMemcpyAsync(nal, (char*)h + pb + bb2, ab, cudaMemcpyHostToDevice, st));
   CK(cudaEventRecord(g.stage_done, st));
 
-  CUtensorMap mY[4], mY4[4], mG[2][4];
-  CKS(tmaps_for(yh, yl, N, B, ld_h, slot_h, mY));
+  // operand planes: Y_n and G as hp = 2^s hi and lo' (split) or hi (plain);
+  // the G planes live in gh (hp or hi) and gl (lo')
+  CUtensorMap mY4[4], mG4[2][4];
   CKS(tmaps4_for(split ? yhp : yh, yl, N, B, ld_h, slot_h, mY4));
-  CKS(tmaps_for(gh[0], gl[0], N, B, ld_h, slot_h, mG[0]));
-  CKS(tmaps_for(gh[1], gl[1], N, B, ld_h, slot_h, mG[1]));
+  CKS(tmaps4_for(gh[0], gl[0], N, B, ld_h, slot_h, mG4[0]));
+  CKS(tmaps4_for(gh[1], gl[1], N, B, ld_h, slot_h, mG4[1]));
   const float ls = std::ldexp(1.0f, g.lo_scale_exp);
   SqArgs A;
   memset(&A, 0, sizeof(A));
@@ -1484,7 +1470,8 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
   auto segY = [&](int i) { return (float*)seg + (size_t)i * B * slot; };
 
   CK(cudaMemcpyAsync(G, G_out, (size_t)B * slot * 4, cudaMemcpyDeviceToDevice, st));
-  CK(launch_split_pad((float*)G, N, slot, N, B, ls, (__half*)gh[0], (__half*)gl[0], nullptr, ld_h, slot_h, sgrid, st));
+  CK(launch_split_pad((float*)G, N, slot, N, B, ls, split ? nullptr : (__half*)gh[0], (__half*)gl[0],
+                      split ? (__half*)gh[0] : nullptr, ld_h, slot_h, sgrid, st));
   int cur = 0;
   const int nseg_layers = (L + ce - 1) / ce;
   for (int sgi = nseg_layers - 1; sgi >= 0; --sgi) {
@@ -1507,12 +1494,15 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
     }
     for (int n = n1 - 1; n >= n0; --n) {
       float* Yn = segY(n - n0);
-      CK(launch_split_pad(Yn, N, slot, N, B, ls, (__half*)yh, (__half*)yl, nullptr, ld_h, slot_h, sgrid, st));
-      CUtensorMap m8[8] = {mY[0], mY[1], mG[cur][2], mG[cur][3], mG[cur][0], mG[cur][1], mY[2], mY[3]};
+      CK(launch_split_pad(Yn, N, slot, N, B, ls, split ? nullptr : (__half*)yh, (__half*)yl,
+                          split ? (__half*)yhp : nullptr, ld_h, slot_h, sgrid, st));
+      // segment 1: Y_n rows x G rows (Y G), segment 2: G rows x Y_n rows (G Y)
+      CUtensorMap m8[8] = {mY4[0], mY4[1], mG4[cur][2], mG4[cur][3], mG4[cur][0], mG4[cur][1], mY4[2], mY4[3]};
       SqArgs Bk = A;
       Bk.Yin = (float*)G;
       Bk.Yout = (float*)G;
-      Bk.hi_out = (__half*)gh[cur ^ 1];
+      Bk.hi_out = split ? nullptr : (__half*)gh[cur ^ 1];
+      Bk.hp_out = split ? (__half*)gh[cur ^ 1] : nullptr;
       Bk.lo_out = (__half*)gl[cur ^ 1];
       Bk.rn = nullptr;
       Bk.lp = (const LayerParams*)params2 + (size_t)n * B;
@@ -1520,7 +1510,7 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
       Bk.aux = Yn;
       Bk.tile_dots = (double*)tdots;
       Bk.dots_out = (double*)dots + (size_t)n * B * 3;
-      CK(launch_syrk_tc(Bk, m8, split, tgrid, st));
+      CK(launch_syrk_tc1(Bk, m8, split, tgrid, st));
       cur ^= 1;
     }
   }

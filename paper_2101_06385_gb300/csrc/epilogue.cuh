@@ -35,8 +35,12 @@ namespace epi {
 constexpr int WARPS = 8;
 constexpr int SLOTS = 4;
 
+// per-warp partials of a tile: tr Y', ||Y'||_F^2 and, in adjoint mode, the
+// three dots (tr Yin, <Yin, aux>, <P, aux>)
+constexpr int NRED = 5;
+
 struct Shared {
-  double red[SLOTS][WARPS][2];
+  double red[SLOTS][WARPS][NRED];
   int cnt[SLOTS];
 };
 
@@ -92,7 +96,10 @@ __device__ __forceinline__ float column_sums_sq(const float (&y)[32], bool valid
 // Tile t with accumulator use `it` (buffer it & 1).  Returns 0 when the
 // tile's instance is inactive (nothing issued for it), 1 when done, -1 when
 // the accumulator wait failed.
-template <bool SPLIT>
+// ADJ (adjoint mode, a.aux set): the tile also accumulates, over its part
+// of the full symmetric matrices, tr Yin, <Yin, aux> and <P, aux> on the
+// old values, summed per instance into a.dots_out.
+template <bool SPLIT, bool ADJ = false>
 __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_t tmem_base, uint64_t* tmem_full,
                                     uint64_t* tmem_empty, volatile int* abort_flag, Shared& sh, int ew, int q,
                                     int lane) {
@@ -142,6 +149,7 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
   const long long ldh = a.ld_h;
   float* D = outD ? a.Dptr[b] : nullptr;
   double tr = 0.0, sq = 0.0;
+  double dtr = 0.0, dgy = 0.0, dpy = 0.0;  // adjoint-mode dots
   const uint32_t taddr = tmem_base + buf * BN + ((uint32_t)(q * 32) << 16) + hc * 128;
   const bool vec_y = (ld & 3) == 0;
 
@@ -189,6 +197,34 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
             yold_d = y[j];
             p_d = __uint_as_float(v[j]) * unscale;
           }
+      }
+      if (ADJ) {
+        // dots on the old values (before the update overwrites y)
+        const float* ax = a.aux + (long long)b * a.slot_y + (long long)r * ld + c0;
+        float gy = 0.f, py = 0.f;
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+          float x[4];
+          if (full_chunk) {
+            const float4 o = reinterpret_cast<const float4*>(ax)[j4];
+            x[0] = o.x;
+            x[1] = o.y;
+            x[2] = o.z;
+            x[3] = o.w;
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = (c0 + 4 * j4 + u < N) ? ax[4 * j4 + u] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = 4 * j4 + u;
+            gy = fmaf(y[j], x[u], gy);
+            py = fmaf(__uint_as_float(v[j]) * unscale, x[u], py);
+          }
+        }
+        dgy += (double)gy;
+        dpy += (double)py;
+        if (dchunk) dtr += (double)yold_d;
       }
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
@@ -289,14 +325,26 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
     }
   }
 
-  if (mirror) sq *= 2.0;
+  if (mirror) {
+    sq *= 2.0;
+    dgy *= 2.0;
+    dpy *= 2.0;
+  }
   tr = warp_sum_d(tr);
   sq = warp_sum_d(sq);
+  if (ADJ) {
+    dtr = warp_sum_d(dtr);
+    dgy = warp_sum_d(dgy);
+    dpy = warp_sum_d(dpy);
+  }
   const int slot = (int)(it & (SLOTS - 1));
   unsigned last = 0;
   if (lane == 0) {
     sh.red[slot][ew][0] = tr;
     sh.red[slot][ew][1] = sq;
+    sh.red[slot][ew][2] = dtr;
+    sh.red[slot][ew][3] = dgy;
+    sh.red[slot][ew][4] = dpy;
     __threadfence_block();
     last = (atomicAdd(&sh.cnt[slot], 1) == WARPS - 1) ? 1u : 0u;
   }
@@ -306,9 +354,18 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
     double T = 0.0, Q = 0.0;
     if (lane == 0) {
       volatile double* rd = &sh.red[slot][0][0];
+      double d0 = 0.0, d1 = 0.0, d2 = 0.0;
       for (int k = 0; k < WARPS; ++k) {
-        T += rd[2 * k];
-        Q += rd[2 * k + 1];
+        T += rd[NRED * k];
+        Q += rd[NRED * k + 1];
+        d0 += rd[NRED * k + 2];
+        d1 += rd[NRED * k + 3];
+        d2 += rd[NRED * k + 4];
+      }
+      if (ADJ) {
+        a.tile_dots[3 * (long long)t + 0] = d0;
+        a.tile_dots[3 * (long long)t + 1] = d1;
+        a.tile_dots[3 * (long long)t + 2] = d2;
       }
       sh.cnt[slot] = 0;
     }

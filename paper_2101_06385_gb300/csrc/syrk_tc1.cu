@@ -43,11 +43,17 @@ constexpr uint32_t TMEM_COLS = 512;  // two 256-column accumulators
 // stage offsets (split): hpA, loA (A_BYTES each), hpB, loB (B_BYTES each)
 constexpr int OFF_HPA = 0, OFF_LOA = A_BYTES, OFF_HPB = 2 * A_BYTES, OFF_LOB = 2 * A_BYTES + B_BYTES;
 
-template <bool SPLIT>
+// NSEG2: P = A_1 B_1^T + A_2 B_2^T over two K segments (the second map set
+// holds the second segment's operands) with the adjoint-mode epilogue: the
+// split SYR2K Y G + G Y of the network adjoint.
+template <bool SPLIT, bool NSEG2>
 __global__ void __launch_bounds__(THREADS, 1)
     syrk_tc1_kernel(const __grid_constant__ CUtensorMap tm_p0A, const __grid_constant__ CUtensorMap tm_p1A,
                     const __grid_constant__ CUtensorMap tm_p0B, const __grid_constant__ CUtensorMap tm_p1B,
+                    const __grid_constant__ CUtensorMap tm2_p0A, const __grid_constant__ CUtensorMap tm2_p1A,
+                    const __grid_constant__ CUtensorMap tm2_p0B, const __grid_constant__ CUtensorMap tm2_p1B,
                     const SqArgs a) {
+  constexpr int NSEG = NSEG2 ? 2 : 1;
   constexpr int STAGES = SPLIT ? STAGES_SPLIT : STAGES_PLAIN;
   constexpr int STAGE_BYTES = SPLIT ? STAGE_SPLIT : STAGE_PLAIN;
 
@@ -106,22 +112,25 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int N = a.Ns[b];
         const int rowA = I * BN + h * BM, rowB = J * BN;
         const int nk = (N + BK - 1) / BK;
-        for (int kb = 0; kb < nk; ++kb) {
+        for (int kb = 0; kb < nk * NSEG; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
             ok = false;
             break;
           }
           uint8_t* st = smem + stage * STAGE_BYTES;
           mbar_expect_tx(&full[stage], STAGE_BYTES);
-          const int k0 = kb * BK;
+          const bool seg2 = NSEG2 && kb >= nk;
+          const int k0 = (seg2 ? kb - nk : kb) * BK;
+          const CUtensorMap* m0A = seg2 ? &tm2_p0A : &tm_p0A;
+          const CUtensorMap* m0B = seg2 ? &tm2_p0B : &tm_p0B;
           if (SPLIT) {
-            tma_load_3d(st + OFF_HPA, &tm_p0A, k0, rowA, b, &full[stage]);
-            tma_load_3d(st + OFF_LOA, &tm_p1A, k0, rowA, b, &full[stage]);
-            tma_load_3d(st + OFF_HPB, &tm_p0B, k0, rowB, b, &full[stage]);
-            tma_load_3d(st + OFF_LOB, &tm_p1B, k0, rowB, b, &full[stage]);
+            tma_load_3d(st + OFF_HPA, m0A, k0, rowA, b, &full[stage]);
+            tma_load_3d(st + OFF_LOA, seg2 ? &tm2_p1A : &tm_p1A, k0, rowA, b, &full[stage]);
+            tma_load_3d(st + OFF_HPB, m0B, k0, rowB, b, &full[stage]);
+            tma_load_3d(st + OFF_LOB, seg2 ? &tm2_p1B : &tm_p1B, k0, rowB, b, &full[stage]);
           } else {
-            tma_load_3d(st, &tm_p0A, k0, rowA, b, &full[stage]);
-            tma_load_3d(st + A_BYTES, &tm_p0B, k0, rowB, b, &full[stage]);
+            tma_load_3d(st, m0A, k0, rowA, b, &full[stage]);
+            tma_load_3d(st + A_BYTES, m0B, k0, rowB, b, &full[stage]);
           }
           ++armed[stage];
           if (++stage == STAGES) {
@@ -160,7 +169,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         tc_fence_after();
         const uint32_t d = tmem_base + buf * BN;
-        for (int kb = 0; kb < nk; ++kb) {
+        for (int kb = 0; kb < nk * NSEG; ++kb) {
           if (!mbar_wait(&full[stage], phase, abort_flag)) {
             ok = false;
             break;
@@ -206,7 +215,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q = warp & 3;   // TMEM lane quarter
     uint32_t it = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-      const int rc = epi::tile<SPLIT>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag, s_epi, ew, q, lane);
+      const int rc =
+          epi::tile<SPLIT, NSEG2>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag, s_epi, ew, q, lane);
       if (rc < 0) break;
       it += (uint32_t)rc;
     }
@@ -228,7 +238,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 namespace {
 template <typename K>
 cudaError_t set_smem_once(K kernel, int bytes, int which) {
-  static int done_dev[2] = {-1, -1};
+  static int done_dev[4] = {-1, -1, -1, -1};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -247,15 +257,31 @@ size_t syrk_tc1_smem_bytes(bool split) {
 
 cudaError_t launch_syrk_tc1(const SqArgs& a, const CUtensorMap* tm, bool split, int grid, cudaStream_t st) {
   const size_t smem = syrk_tc1_smem_bytes(split);
+  // the second map set: segment 2 of the two-segment product, else unused
+  const CUtensorMap* t2 = (a.nseg == 2) ? tm + 4 : tm;
   cudaError_t e;
-  if (split) {
-    e = set_smem_once(tc1::syrk_tc1_kernel<true>, (int)smem, 1);
+  if (a.nseg == 2) {
+    if (split) {
+      e = set_smem_once(tc1::syrk_tc1_kernel<true, true>, (int)smem, 2);
+      if (e != cudaSuccess) return e;
+      tc1::syrk_tc1_kernel<true, true><<<grid, tc1::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], t2[0], t2[1],
+                                                                          t2[2], t2[3], a);
+    } else {
+      e = set_smem_once(tc1::syrk_tc1_kernel<false, true>, (int)smem, 3);
+      if (e != cudaSuccess) return e;
+      tc1::syrk_tc1_kernel<false, true><<<grid, tc1::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], t2[0], t2[1],
+                                                                           t2[2], t2[3], a);
+    }
+  } else if (split) {
+    e = set_smem_once(tc1::syrk_tc1_kernel<true, false>, (int)smem, 1);
     if (e != cudaSuccess) return e;
-    tc1::syrk_tc1_kernel<true><<<grid, tc1::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], a);
+    tc1::syrk_tc1_kernel<true, false><<<grid, tc1::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], t2[0], t2[1],
+                                                                         t2[2], t2[3], a);
   } else {
-    e = set_smem_once(tc1::syrk_tc1_kernel<false>, (int)smem, 0);
+    e = set_smem_once(tc1::syrk_tc1_kernel<false, false>, (int)smem, 0);
     if (e != cudaSuccess) return e;
-    tc1::syrk_tc1_kernel<false><<<grid, tc1::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], a);
+    tc1::syrk_tc1_kernel<false, false><<<grid, tc1::THREADS, smem, st>>>(tm[0], tm[1], tm[2], tm[3], t2[0], t2[1],
+                                                                          t2[2], t2[3], a);
   }
   return cudaGetLastError();
 }
