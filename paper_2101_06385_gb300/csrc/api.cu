@@ -1253,7 +1253,10 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
     CK(cudaMemcpy2DAsync(bounds, 2 * sizeof(double), (char*)ctl + offsetof(Ctl, e_min), sizeof(Ctl),
                          2 * sizeof(double), B, cudaMemcpyDeviceToDevice, st));
   int ntiles = 0;
-  CKS(upload_tiles(N, B, tc ? 1 : 0, &ntiles));
+  // tensor-core layers on CTA pairs (super-tile pairs sharing B) unless
+  // single CTAs are selected, as for the single solve
+  const bool pairs = tc && g.pair_kernel;
+  CKS(upload_tiles(N, B, tc ? (pairs ? 2 : 1) : 0, &ntiles));
   void *params, *alpha, *rn, *part, *tick, *err;
   CKS(ws(B_PARAMS, plan.params.size() * sizeof(LayerParams), &params));
   CKS(ws(B_BOUNDS, plan.alpha.size() * sizeof(double), &alpha));
@@ -1305,8 +1308,9 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
     slot_h = ld_h * N;
     CKS(planes_for(split, 0, (size_t)slot_h * B * 2, &hi[0], &lo[0], &hp[0]));
     CKS(planes_for(split, 1, (size_t)slot_h * B * 2, &hi[1], &lo[1], &hp[1]));
-    CKS(tmaps4_for(split ? hp[0] : hi[0], lo[0], N, B, ld_h, slot_h, m[0]));
-    CKS(tmaps4_for(split ? hp[1] : hi[1], lo[1], N, B, ld_h, slot_h, m[1]));
+    const int boxb = pairs ? kTcBM : kTcBN;
+    CKS(tmaps4_for(split ? hp[0] : hi[0], lo[0], N, B, ld_h, slot_h, m[0], boxb));
+    CKS(tmaps4_for(split ? hp[1] : hi[1], lo[1], N, B, ld_h, slot_h, m[1], boxb));
     A.ld_h = ld_h;
     A.slot_h = slot_h;
   } else {
@@ -1338,7 +1342,10 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
       A.lo_out = (__half*)lo[cur ^ 1];
       A.hp_out = (__half*)hp[cur ^ 1];
       rnp_step(A, rnp, n);
-      CK(launch_syrk_tc1(A, m[cur], split, std::min(ntiles, g.num_sms), st));
+      if (pairs)
+        CK(launch_syrk_tc2(A, m[cur], split, std::min(ntiles, g.num_sms) & ~1, st));
+      else
+        CK(launch_syrk_tc1(A, m[cur], split, std::min(ntiles, g.num_sms), st));
     } else {
       A.Yin = Yc;
       A.Yout = (float*)Y[cur ^ 1];
