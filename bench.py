@@ -519,6 +519,7 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "no flush: inputs (1 GiB FP32 H, 1.5 GiB iterate + splits) larger than L2",
                    "time_to_D_ms": ms, "layers": layers, "loop_layers": st.iterations,
+                   "prologue_ms": st.prologue_ms,
                    "converged_by": st.converged_by, "generator_s": round(t_gen, 1),
                    "paper_convention_tflops": st.iterations * 4.0 * N ** 3 / (sum(
                        st.layer_ms[: st.iterations]) * 1e-3) / 1e12},

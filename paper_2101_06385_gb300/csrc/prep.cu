@@ -33,13 +33,25 @@ __global__ void __launch_bounds__(256) gershgorin_kernel(const float* __restrict
     const float* row = H + (long long)b * slot + (long long)i * ld;
     double acc = 0.0;
     if (vec) {
+      // four independent loads and FP64 accumulators per step (the FP64
+      // adds would otherwise serialise the row)
       const float4* r4 = reinterpret_cast<const float4*>(row);
       const int n4 = N >> 2;
-      for (int j = lane; j < n4; j += 32) {
-        const float4 v = __ldcs(r4 + j);
-        acc += (double)((fabsf(v.x) + fabsf(v.y)) + (fabsf(v.z) + fabsf(v.w)));
+      double a4[4] = {0.0, 0.0, 0.0, 0.0};
+      int j = lane;
+      for (; j + 96 < n4; j += 128) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = __ldcs(r4 + j + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a4[u] += (double)((fabsf(v[u].x) + fabsf(v[u].y)) + (fabsf(v[u].z) + fabsf(v[u].w)));
       }
-      for (int j = (n4 << 2) + lane; j < N; j += 32) acc += (double)fabsf(row[j]);
+      for (; j < n4; j += 32) {
+        const float4 v = __ldcs(r4 + j);
+        a4[0] += (double)((fabsf(v.x) + fabsf(v.y)) + (fabsf(v.z) + fabsf(v.w)));
+      }
+      acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+      for (int jj = (n4 << 2) + lane; jj < N; jj += 32) acc += (double)fabsf(row[jj]);
     } else {
       for (int j = lane; j < N; j += 32) acc += (double)fabsf(row[j]);
     }
@@ -237,12 +249,83 @@ __global__ void __launch_bounds__(256) input_layer_kernel(const float* const* __
   }
   const double inv = 1.0 / (e_max - e_min);
   const double diag_add = shift ? 0.0 : e_max * inv;
+  // off-diagonal y = -h inv in FP32: inv as a sum of two floats and one FMA
+  // (-h inv_hi + (-h inv_lo) rounded once), the correctly rounded FP64 value
+  // except within 2^-47 of a rounding boundary; the diagonal stays in FP64
+  const float inv_hi = (float)inv, inv_lo = (float)(inv - (double)inv_hi);
   double tr = 0.0, sq = 0.0;
   if (active) {
     // FP16 planes: hi (plain), or hp = 2^s hi and lo' (split); hi may be absent
     const bool halves = (hi != nullptr) || (hp != nullptr);
     const int rows = halves ? rows_pad : N;
     const int cols = halves ? cols_pad : N;
+    const bool vec = ((ld_in & 3) == 0) && ((ld_y & 3) == 0) && ((slot_y & 3) == 0) && ((((uintptr_t)H) & 15) == 0) &&
+                     ((((uintptr_t)Y) & 15) == 0) && (!halves || ((ld_h & 3) == 0 && (slot_h & 3) == 0));
+    if (vec) {
+      // four consecutive columns per thread: float4 loads and stores, 8-byte plane stores
+      for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const float* hrow = H + (long long)r * ld_in;
+        float* yrow = Y + (long long)b * slot_y + (long long)r * ld_y;
+        __half* hirow = hi ? hi + (long long)b * slot_h + (long long)r * ld_h : nullptr;
+        __half* lorow = (halves && lo) ? lo + (long long)b * slot_h + (long long)r * ld_h : nullptr;
+        __half* hprow = hp ? hp + (long long)b * slot_h + (long long)r * ld_h : nullptr;
+        float sqf = 0.f;
+        for (int c4 = threadIdx.x * 4; c4 < cols; c4 += blockDim.x * 4) {
+          float y[4] = {0.f, 0.f, 0.f, 0.f};
+          if (r < N) {
+            float hv[4];
+            if (c4 + 3 < N) {
+              const float4 o = __ldcs(reinterpret_cast<const float4*>(hrow + c4));
+              hv[0] = o.x;
+              hv[1] = o.y;
+              hv[2] = o.z;
+              hv[3] = o.w;
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) hv[u] = (c4 + u < N) ? hrow[c4 + u] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int col = c4 + u;
+              if (col < N) {
+                if (col == r) {
+                  const double v = -(double)hv[u] * inv + diag_add;
+                  y[u] = (float)v;
+                  tr += (double)y[u];
+                } else {
+                  y[u] = fmaf(-hv[u], inv_hi, -hv[u] * inv_lo);
+                }
+                sqf = fmaf(y[u], y[u], sqf);
+              }
+            }
+            if (c4 + 3 < N) {
+              *reinterpret_cast<float4*>(yrow + c4) = make_float4(y[0], y[1], y[2], y[3]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (c4 + u < N) yrow[c4 + u] = y[u];
+            }
+          }
+          if (halves) {
+            __half h16[4], l16[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) split_fp16(y[u], lo_scale, h16[u], l16[u]);
+            auto pk = [](__half x0, __half x1) {
+              return (uint32_t)__half_as_ushort(x0) | ((uint32_t)__half_as_ushort(x1) << 16);
+            };
+            if (hirow) *reinterpret_cast<uint2*>(hirow + c4) = make_uint2(pk(h16[0], h16[1]), pk(h16[2], h16[3]));
+            if (lorow) *reinterpret_cast<uint2*>(lorow + c4) = make_uint2(pk(l16[0], l16[1]), pk(l16[2], l16[3]));
+            if (hprow) {
+              __half p16[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) p16[u] = __float2half_rn(__half2float(h16[u]) * lo_scale);
+              *reinterpret_cast<uint2*>(hprow + c4) = make_uint2(pk(p16[0], p16[1]), pk(p16[2], p16[3]));
+            }
+          }
+        }
+        sq += (double)sqf;
+      }
+    } else
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
       const float* hrow = H + (long long)r * ld_in;
       float* yrow = Y + (long long)b * slot_y + (long long)r * ld_y;
@@ -253,9 +336,11 @@ __global__ void __launch_bounds__(256) input_layer_kernel(const float* const* __
       for (int col = threadIdx.x; col < cols; col += blockDim.x) {
         float y = 0.f;
         if (r < N && col < N) {
-          double v = -(double)hrow[col] * inv;
-          if (r == col) v += diag_add;
-          y = (float)v;
+          const float hv = hrow[col];
+          if (r == col)
+            y = (float)(-(double)hv * inv + diag_add);
+          else
+            y = fmaf(-hv, inv_hi, -hv * inv_lo);
           yrow[col] = y;
           if (r == col) tr += (double)y;
           sqf = fmaf(y, y, sqf);
