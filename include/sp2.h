@@ -97,10 +97,13 @@ typedef struct {
                                      iterations + 2 find the solve finished and return at once */
   int8_t sigma[SP2_MAX_LAYERS];   /* sigma[k] = sigma_{k+1} in {+1,-1}; 0 past the end */
   double iderr[SP2_MAX_LAYERS];   /* iderr[k] = IdErr_{k+1} */
-  float layer_ms[SP2_MAX_LAYERS]; /* device time of layer k (k < launches): squaring launch plus
-                                     its row-norm pass; the loop layers, then the two refinement
-                                     layers of Eq. 15 */
+  float layer_ms[SP2_MAX_LAYERS]; /* device time of layer k (k < launches): the loop layers, then
+                                     the two refinement layers of Eq. 15 (one squaring launch per
+                                     layer on the tensor-core path; launch plus row-norm pass on
+                                     the FFMA path) */
   float square_ms[SP2_MAX_LAYERS];/* device time of squaring launch k alone */
+  double energy;                  /* Tr[D H] (Alg. 1, last line), accumulated by the launch that
+                                     writes D (tensor-core path; 0 on the FFMA path) */
 } sp2_stats;
 
 /* Library set-up.  cfg == NULL selects the defaults {device 0, NULL stream,

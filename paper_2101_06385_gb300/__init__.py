@@ -92,6 +92,7 @@ class _Stats(ctypes.Structure):
         ("iderr", ctypes.c_double * SP2_MAX_LAYERS),
         ("layer_ms", ctypes.c_float * SP2_MAX_LAYERS),
         ("square_ms", ctypes.c_float * SP2_MAX_LAYERS),
+        ("energy", ctypes.c_double),
     ]
 
 
@@ -113,6 +114,7 @@ class Stats:
     launches: int = 0
     layer_ms: List[float] = dataclasses.field(default_factory=list)
     square_ms: List[float] = dataclasses.field(default_factory=list)
+    energy: float = 0.0
 
     @property
     def converged(self) -> bool:
@@ -231,7 +233,7 @@ def _stats(s: _Stats, status: int) -> Stats:
                  time_ms=s.time_ms, flops_alg=s.flops_alg, sigmas=[int(v) for v in s.sigma[:n]],
                  iderr=[float(v) for v in s.iderr[:n]], prologue_ms=s.prologue_ms, launches=s.launches,
                  layer_ms=[float(v) for v in s.layer_ms[:s.launches]],
-                 square_ms=[float(v) for v in s.square_ms[:s.launches]])
+                 square_ms=[float(v) for v in s.square_ms[:s.launches]], energy=float(s.energy))
 
 
 def _stats_many(st, B: int) -> List[Stats]:
@@ -239,7 +241,7 @@ def _stats_many(st, B: int) -> List[Stats]:
     view of the ctypes records (per-element ctypes access would dominate)."""
     a = np.ctypeslib.as_array(st)
     col = {k: a[k].tolist() for k in ("iterations", "launches", "converged_by", "e_min", "e_max", "idemp_err",
-                                       "trace", "alpha", "time_ms", "flops_alg", "prologue_ms")}
+                                       "trace", "alpha", "time_ms", "flops_alg", "prologue_ms", "energy")}
     nmax = max(col["iterations"]) if B else 0
     lmax = max(col["launches"]) if B else 0
     sig = a["sigma"][:, :nmax].tolist()
@@ -258,7 +260,7 @@ def _stats_many(st, B: int) -> List[Stats]:
                          trace=col["trace"][i], alpha=col["alpha"][i], time_ms=col["time_ms"][i],
                          flops_alg=col["flops_alg"][i], sigmas=sig[i][:n], iderr=ide[i][:n],
                          prologue_ms=col["prologue_ms"][i], launches=nl, layer_ms=lms[i][:nl],
-                         square_ms=sms[i][:nl]))
+                         square_ms=sms[i][:nl], energy=col["energy"][i]))
     return out
 
 

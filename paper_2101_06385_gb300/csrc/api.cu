@@ -635,6 +635,10 @@ sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int
   CKS(ws(B_TICKET, 64 * sizeof(unsigned), &tick, true));
   void* rn;
   CKS(ws(B_RN, (size_t)N * sizeof(double), &rn));
+  // Tr[D H] from the launch that writes D: per-tile partials, then the sum
+  void *tdots, *dots;
+  CKS(ws(B_TDOTS, (size_t)ntiles * 3 * sizeof(double), &tdots));
+  CKS(ws(B_DOTS, 3 * sizeof(double), &dots, true));
 
   // small per-call records through pinned staging
   void* h;
@@ -680,6 +684,11 @@ sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int
   A.err = (int*)err;
   A.rn = (const double*)rn;
   A.ld_rn = N;
+  if (tc) {
+    A.Hobs = (const float* const*)hs;
+    A.tile_dots = (double*)tdots;
+    A.dots_out = (double*)dots;
+  }
 
   CK(cudaEventRecord(g.ev0, st));
   CK(launch_gershgorin(H, N, N, (long long)N * N, 1, (double2*)part, (unsigned*)tick, (Ctl*)ctl, nullptr, ggrid, st));
@@ -756,9 +765,10 @@ sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int
 
   if (!stats) return SP2_OK;
   void* hb;
-  CKS(staging(sizeof(Ctl) + 16, &hb));
+  CKS(staging(sizeof(Ctl) + 64, &hb));
   CK(cudaMemcpyAsync(hb, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync((char*)hb + sizeof(Ctl), err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync((char*)hb + sizeof(Ctl) + 16, dots, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, g.ev0, g.ev1));
@@ -766,6 +776,7 @@ sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int
   const int e = *(const int*)((char*)hb + sizeof(Ctl));
   fill_stats(c, stats, ms, prec);
   stats->launches = nlaunch;
+  if (tc) stats->energy = *(const double*)((const char*)hb + sizeof(Ctl) + 16);
   float pm = 0.f;
   CK(cudaEventElapsedTime(&pm, g.ev0, g.lev[0]));
   stats->prologue_ms = pm;
@@ -863,6 +874,9 @@ sp2_status batched_once(const float* const* H, const int* N, const int* N_occ, i
   CKS(ws(B_PART, (size_t)B * std::max(igrid, rgrid) * sizeof(double2), &part));
   CKS(ws(B_TICKET, std::max(64, B) * sizeof(unsigned), &tick, true));
   CKS(ws(B_RN, (size_t)B * Nmax * sizeof(double), &rn));
+  void *tdots, *dots;
+  CKS(ws(B_TDOTS, (size_t)nt * 3 * sizeof(double), &tdots));
+  CKS(ws(B_DOTS, (size_t)B * 3 * sizeof(double), &dots, true));
 
   // per-call records through pinned staging
   const size_t bytes = (size_t)B * sizeof(Ctl) + nt * sizeof(uint32_t) + 2 * B * sizeof(int) + B * sizeof(int) +
@@ -911,6 +925,12 @@ sp2_status batched_once(const float* const* H, const int* N, const int* N_occ, i
   A.lo_scale = std::ldexp(1.0f, g.lo_scale_exp);
   A.lo_unscale = std::ldexp(1.0f, -g.lo_scale_exp);
   A.err = (int*)err;
+  if (tc) {
+    // Tr[D H] per instance from the launch that writes D
+    A.Hobs = (const float* const*)hs;
+    A.tile_dots = (double*)tdots;
+    A.dots_out = (double*)dots;
+  }
 
   // workspace and tensor maps first: the launch sequence below makes only
   // stream operations, so it can be captured into a CUDA graph
@@ -1010,7 +1030,7 @@ sp2_status batched_once(const float* const* H, const int* N, const int* N_occ, i
                             (uint64_t)(uintptr_t)Y[0], (uint64_t)(uintptr_t)Y[1], (uint64_t)(uintptr_t)hi[0],
                             (uint64_t)(uintptr_t)hi[1], (uint64_t)(uintptr_t)lo[0], (uint64_t)(uintptr_t)lo[1],
                             (uint64_t)(uintptr_t)hp[0], (uint64_t)(uintptr_t)hp[1], (uint64_t)(uintptr_t)rnp[0],
-                            (uint64_t)(uintptr_t)rnp[1]};
+                            (uint64_t)(uintptr_t)rnp[1], (uint64_t)(uintptr_t)tdots, (uint64_t)(uintptr_t)dots};
     std::vector<uint64_t> kv(key, key + sizeof(key) / sizeof(key[0]));
     if (!g.bgraph || g.bgraph_key != kv) {
       if (g.bgraph) {
@@ -1110,9 +1130,12 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   void* err = g.buf[B_ERR].p;
 
   void* hb;
-  CKS(staging((size_t)B * sizeof(Ctl) + 16, &hb));
+  const size_t eoff = (size_t)B * sizeof(Ctl) + 16;
+  CKS(staging(eoff + (size_t)B * 3 * sizeof(double), &hb));
   CK(cudaMemcpyAsync(hb, ctl, (size_t)B * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync((char*)hb + (size_t)B * sizeof(Ctl), err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (tc) CK(cudaMemcpyAsync((char*)hb + eoff, g.buf[B_DOTS].p, (size_t)B * 3 * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, g.ev0, g.ev1));
@@ -1128,6 +1151,7 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   for (int b = 0; b < B; ++b) {
     fill_stats(cs[b], &stats[b], ms, prec);
     stats[b].launches = max_iter + 2;
+    if (tc) stats[b].energy = ((const double*)((const char*)hb + eoff))[3 * b];
     stats[b].prologue_ms = pro;
     for (int k = 0; k < max_iter + 2; ++k) {
       stats[b].layer_ms[k] = lms[k];

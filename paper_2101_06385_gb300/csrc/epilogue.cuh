@@ -149,7 +149,8 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
   const long long ldh = a.ld_h;
   float* D = outD ? a.Dptr[b] : nullptr;
   double tr = 0.0, sq = 0.0;
-  double dtr = 0.0, dgy = 0.0, dpy = 0.0;  // adjoint-mode dots
+  // adjoint-mode dots; dtr carries the Tr[D A] partial in the launch that writes D
+  double dtr = 0.0, dgy = 0.0, dpy = 0.0;
   const uint32_t taddr = tmem_base + buf * BN + ((uint32_t)(q * 32) << 16) + hc * 128;
   const bool vec_y = (ld & 3) == 0;
 
@@ -253,6 +254,32 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
 #pragma unroll
         for (int j = 0; j < 32; ++j)
           if (c0 + j < N) D[(long long)r * N + c0 + j] = (dchunk && j == jd) ? ydo : y[j];
+        if (!ADJ && a.Hobs) {
+          // Tr[D A] over this row segment (A symmetric: the mirror counts twice below)
+          const float* hr = a.Hobs[b] + (long long)r * N + c0;
+          const bool hvec = ((N & 3) == 0) && (c0 + 32 <= N) && ((((uintptr_t)a.Hobs[b]) & 15) == 0);
+          float eo = 0.f;
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4) {
+            float x[4];
+            if (hvec) {
+              const float4 o = reinterpret_cast<const float4*>(hr)[j4];
+              x[0] = o.x;
+              x[1] = o.y;
+              x[2] = o.z;
+              x[3] = o.w;
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) x[u] = (c0 + 4 * j4 + u < N) ? hr[4 * j4 + u] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int j = 4 * j4 + u;
+              eo = fmaf((dchunk && j == jd) ? ydo : y[j], x[u], eo);
+            }
+          }
+          dtr += (double)eo;
+        }
       } else {
         if (full_chunk) {
           float4* dst = reinterpret_cast<float4*>(Y + (long long)r * ld + c0);
@@ -325,14 +352,16 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
     }
   }
 
+  const bool energy = !ADJ && outD && a.Hobs;  // dtr holds the Tr[D A] partial
   if (mirror) {
     sq *= 2.0;
     dgy *= 2.0;
     dpy *= 2.0;
+    if (energy) dtr *= 2.0;
   }
   tr = warp_sum_d(tr);
   sq = warp_sum_d(sq);
-  if (ADJ) {
+  if (ADJ || energy) {
     dtr = warp_sum_d(dtr);
     dgy = warp_sum_d(dgy);
     dpy = warp_sum_d(dpy);
@@ -362,7 +391,7 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
         d1 += rd[NRED * k + 3];
         d2 += rd[NRED * k + 4];
       }
-      if (ADJ) {
+      if (ADJ || energy) {
         a.tile_dots[3 * (long long)t + 0] = d0;
         a.tile_dots[3 * (long long)t + 1] = d1;
         a.tile_dots[3 * (long long)t + 2] = d2;

@@ -53,6 +53,8 @@ struct SqArgs {
   int fused_ctl;           // 1: the last tile of an instance runs its control step with
                            //    (tr Y', ||Y'||_F^2) from the tiles (no row-norm launch)
   int nseg;                // 1: P = Y Y (one operand); 2: P = A B^T + B A^T (second map set)
+  const float* const* Hobs; // [batch] N x N matrices A: the launch that writes D (OUT_D) also
+                            // accumulates Tr[D A] per instance into dots_out[3 b] (or nullptr)
   const float* aux;        // adjoint mode: Y_n, same layout as Yin; dots <P, aux>, <Yin, aux>
   double* tile_dots;       // [ntiles][3] per-tile (tr Yin, <Yin, aux>, <P, aux>) in adjoint mode
   double* dots_out;        // [batch][3] per-instance sums of tile_dots

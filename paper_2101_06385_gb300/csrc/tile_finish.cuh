@@ -36,7 +36,9 @@ __device__ inline void finish_tile_warp(const SqArgs& a, int t, int b, double tr
   T = warp_sum_d(T);
   Q = warp_sum_d(Q);
   double d0 = 0.0, d1 = 0.0, d2 = 0.0;
-  if (a.dots_out) {
+  // per-tile dots exist in adjoint mode and, for Tr[D A], in the launch that writes D
+  const bool dots = a.dots_out && (a.aux || (a.Hobs && out_mode == OUT_D));
+  if (dots) {
     for (int k = lane; k < cnt; k += 32) {
       const double* td = a.tile_dots + 3 * (long long)(off + k);
       d0 += __ldcg(td);
@@ -48,7 +50,7 @@ __device__ inline void finish_tile_warp(const SqArgs& a, int t, int b, double tr
     d2 = warp_sum_d(d2);
   }
   if (lane == 0) {
-    if (a.dots_out) {
+    if (dots) {
       a.dots_out[3 * b + 0] = d0;
       a.dots_out[3 * b + 1] = d1;
       a.dots_out[3 * b + 2] = d2;

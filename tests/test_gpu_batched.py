@@ -141,3 +141,14 @@ def test_schedules_agree(sp2, sizes):
     Dt, _ = sp2.density_matrix_batched(Hs, n_occ)
     for a, b in zip(out["single"][0], Dt):
         assert torch.equal(a, b)
+
+
+def test_batched_fused_energy(sp2):
+    sizes = [64, 300, 1000, 5, 257]
+    hs = [si.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), seed=950 + i) for i, N in enumerate(sizes)]
+    Hs = [torch.from_numpy(h.h32()).cuda() for h in hs]
+    Ds, stats = sp2.density_matrix_batched(Hs, [h.n_occ for h in hs])
+    for h, H, D, st in zip(hs, Hs, Ds, stats):
+        scale = np.sum(np.abs(h.eps))
+        assert abs(st.energy - sp2.observable(D, H)) <= 1e-6 * scale
+        assert abs(st.energy - float(np.sum(np.sort(h.eps)[: h.n_occ]))) <= 1e-5 * scale

@@ -113,3 +113,20 @@ def test_max_iter_reports_not_converged(sp2):
     h = si.gapped_hamiltonian(300, 150, seed=2)
     D, st = _solve(sp2, h, "split", max_iter=5)
     assert st.status == 1 and st.iterations == 5 and st.converged_by == "max_iter"
+
+
+@pytest.mark.parametrize("N", [257, 1000])
+def test_fused_energy(sp2, N):
+    """Tr[D H] (Alg. 1, last line) accumulated by the launch that writes D
+    equals the observable of the returned D and the exact band energy."""
+    h = si.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), seed=50 + N)
+    H = torch.from_numpy(h.h32()).cuda()
+    D, st = sp2.density_matrix(H, h.n_occ, precision="split")
+    e_obs = sp2.observable(D, H)
+    e_exact = float(np.sum(np.sort(h.eps)[: h.n_occ]))
+    print(f"N={N}: fused {st.energy:.9f} observable {e_obs:.9f} exact {e_exact:.9f}")
+    assert abs(st.energy - e_obs) <= 1e-6 * np.sum(np.abs(h.eps))
+    assert abs(st.energy - e_exact) <= 1e-5 * np.sum(np.abs(h.eps))
+    Da, sa = sp2.density_matrix_accelerated(H, h.n_occ, float(np.max(h.eps[: h.n_occ])),
+                                            float(np.min(h.eps[h.n_occ:])))
+    assert abs(sa.energy - sp2.observable(Da, H)) <= 1e-6 * np.sum(np.abs(h.eps))
