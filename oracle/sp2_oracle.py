@@ -31,6 +31,12 @@ accelerated_layer              fixed points and fold of each layer polynomial;
                                bounds enclose the true eigenvalue images
 sp2_accelerated                closed form Q_occ Q_occ^T; layer-count reduction
                                against sp2 (Fig. AccConv trend)
+fermi_expansion_scalar         identity layers (F = 1 - eps); SP2 branch layers
+                               reproduce the scalar SP2 map
+fermi_expansion_matrix         Q diag(fermi_expansion_scalar(eps)) Q^T from the
+                               generator's eigenpairs
+fit_fermi_expansion            max error against the Fermi-Dirac function on a
+                               fine grid (Fig. 6 set-up: beta 40, 11 layers)
 =============================  =================================================
 
 Readings of points the paper leaves open (same list as the design notes):
@@ -56,6 +62,15 @@ C20 the accelerated scheme stops once max(l, 1 - h) <= tol (a bound on the
     eigenvalue distance of the iterate from 0 and 1); no f_final follows.
 C21 HOMO/LUMO energies are caller estimates; they are safe when the gap they
     span lies inside the true one (homo >= true HOMO, lumo <= true LUMO).
+C22 finite-temperature expansion (Sec. "Optimized SP2 Finite Temperature
+    Fermi-Operator Expansion"): the scaled energy eps = (E - e_lo)/(e_hi - e_lo)
+    maps the spectrum bounds to [0, 1]; the readout F~ = 1 - sum_i c_i eps_i
+    includes eps_0 and every layer's output; the matrix form is
+    D = I - sum_i c_i X_i with X_0 the scaled H.
+C23 the fit: uniform weights on a uniform grid of [0, 1], Levenberg-Marquardt
+    from a fixed start (an affine layer that places 1/2 on the fixed point of
+    the alternating SP2 pair, then the SP2 branch polynomials, readout on the
+    last layer); the paper's own start and grid are not given.
 """
 from __future__ import annotations
 
@@ -66,6 +81,10 @@ from typing import List, Optional, Sequence, Tuple
 import numpy as np
 
 __all__ = [
+    "fermi_expansion_scalar",
+    "fermi_expansion_matrix",
+    "fermi_dirac_scaled",
+    "fit_fermi_expansion",
     "accelerated_layer",
     "sp2_accelerated",
     "AccelResult",
@@ -290,6 +309,78 @@ def sp2_accelerated(H: np.ndarray, n_occ: int, homo: float, lumo: float, tol: fl
         coef.append((a, b, c))
         hist.append((l, h))
     return AccelResult(D=S, n_layers=n, sigmas=sig, coefficients=coef, bounds=hist, e_min=e_min, e_max=e_max)
+
+
+def fermi_expansion_scalar(theta: np.ndarray, c: np.ndarray, eps) -> np.ndarray:
+    """The generalised SP2 layers on a scalar and their readout (Sec.
+    "Optimized SP2 Finite Temperature Fermi-Operator Expansion"):
+        eps_0 = eps,  eps_n = theta[n-1, 0] eps_{n-1}^2 + theta[n-1, 1] eps_{n-1} + theta[n-1, 2],
+        F~(eps) = 1 - sum_{i=0}^{L} c_i eps_i     (L = len(theta), len(c) = L + 1).
+    """
+    theta = np.asarray(theta, dtype=np.float64)
+    c = np.asarray(c, dtype=np.float64)
+    e = np.asarray(eps, dtype=np.float64)
+    acc = c[0] * e
+    with np.errstate(over="ignore", invalid="ignore"):
+        for n in range(theta.shape[0]):
+            e = theta[n, 0] * e * e + theta[n, 1] * e + theta[n, 2]
+            acc = acc + c[n + 1] * e
+    return 1.0 - acc
+
+
+def fermi_expansion_matrix(H: np.ndarray, theta: np.ndarray, c: np.ndarray,
+                           bounds: Tuple[float, float]) -> np.ndarray:
+    """Matrix form of ``fermi_expansion_scalar`` (reading C22):
+    X_0 = (H - e_lo I)/(e_hi - e_lo), X_n = a X_{n-1}^2 + b X_{n-1} + c I,
+    D = I - sum_i c_i X_i."""
+    H = np.asarray(H, dtype=np.float64)
+    N = H.shape[0]
+    e_lo, e_hi = bounds
+    I = np.eye(N)
+    X = (H - e_lo * I) / (e_hi - e_lo)
+    R = c[0] * X
+    for n in range(np.asarray(theta).shape[0]):
+        a, b, cc = theta[n]
+        X = a * (X @ X) + b * X + cc * I
+        R = R + c[n + 1] * X
+    return I - R
+
+
+def fermi_dirac_scaled(eps, beta: float) -> np.ndarray:
+    """F(eps) = 1/(exp(beta (eps - 1/2)) + 1) on the scaled energy axis (Eq. 19)."""
+    e = np.asarray(eps, dtype=np.float64)
+    with np.errstate(over="ignore"):
+        return 1.0 / (np.exp(beta * (e - 0.5)) + 1.0)
+
+
+def fit_fermi_expansion(beta: float = 40.0, layers: int = 11, n_grid: int = 2001, max_nfev: int = 20000):
+    """Least-squares fit of theta [layers, 3] and c [layers + 1] so that
+    ``fermi_expansion_scalar`` matches ``fermi_dirac_scaled`` on a uniform grid
+    of [0, 1] (uniform weights), by Levenberg-Marquardt (readings C22, C23).
+    Returns (theta, c, max_abs_error_on_grid)."""
+    from scipy.optimize import least_squares  # library optimiser (test infrastructure)
+
+    L = int(layers)
+    grid = np.linspace(0.0, 1.0, n_grid)
+    target = fermi_dirac_scaled(grid, beta)
+    p = (math.sqrt(5.0) - 1.0) / 2.0          # fixed point of (2x - x^2) o x^2
+    s = min(2.0 * p, 2.0 * (1.0 - p))
+    theta0 = np.zeros((L, 3))
+    theta0[0] = (0.0, s, p - 0.5 * s)         # 1/2 -> p, [0, 1] -> [p - s/2, p + s/2]
+    for n in range(1, L):
+        theta0[n] = (-1.0, 2.0, 0.0) if n % 2 == 1 else (1.0, 0.0, 0.0)
+    c0 = np.zeros(L + 1)
+    c0[L] = 1.0
+
+    def resid(x):
+        r = fermi_expansion_scalar(x[: 3 * L].reshape(L, 3), x[3 * L:], grid) - target
+        return np.nan_to_num(r, nan=1e3, posinf=1e3, neginf=-1e3)
+
+    r = least_squares(resid, np.concatenate([theta0.ravel(), c0]), method="lm", xtol=1e-15, ftol=1e-15,
+                      gtol=1e-15, max_nfev=max_nfev)
+    theta = r.x[: 3 * L].reshape(L, 3)
+    c = r.x[3 * L:]
+    return theta, c, float(np.max(np.abs(fermi_expansion_scalar(theta, c, grid) - target)))
 
 
 def f_final(S: np.ndarray, sigma_nm2: int) -> np.ndarray:
