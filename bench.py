@@ -61,7 +61,7 @@ def _args():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-SP2 measurement")
     ap.add_argument("--no-network", action="store_true", help="skip the network forward/backward measurement")
     ap.add_argument("--no-accel", action="store_true", help="skip the accelerated-layer measurement")
-    ap.add_argument("--only", default=None, choices=["batched", "network"],
+    ap.add_argument("--only", default=None, choices=["batched", "network", "fermi"],
                     help="run one secondary measurement alone and print it (profiling runs)")
     ap.add_argument("--batched-count", type=int, default=512)
     return ap.parse_args()
@@ -329,6 +329,31 @@ def _bench_network(sp2, sp2_inputs, dev, B=64, N=2048, L=20, ckpt_every=5, reps=
             "forward_tflops_alg": f_fwd / (fwd * 1e-3) / 1e12, "backward_tflops_alg": f_bwd / (bwd * 1e-3) / 1e12}
 
 
+def _bench_fermi(sp2, sp2_inputs, dev, B=64, N=2048, L=11, reps=3):
+    """Finite-temperature expansion (11 generalised layers with the readout
+    fused into the squaring epilogue) on the network workload's 64 instances
+    of N = 2048.  The timing does not depend on the coefficient values; the
+    SP2 branch polynomials with the readout on the last layer are used."""
+    import torch
+
+    Hs = [sp2_inputs.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), 2000 + i, device=str(dev)).h32()
+          for i in range(B)]
+    H = torch.from_numpy(np.stack(Hs)).to(dev)
+    theta = np.array([[1.0, 0.0, 0.0] if n % 2 else [-1.0, 2.0, 0.0] for n in range(L)])
+    c = np.zeros(L + 1)
+    c[-1] = 1.0
+    D, _ = sp2.fermi_expansion(H, theta, c)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        sp2.fermi_expansion(H, theta, c, out=D)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    return {"B": B, "N": N, "layers": L, "ms": ms, "tflops_alg": B * L * 3.0 * N ** 3 / (ms * 1e-3) / 1e12}
+
+
 def run_ours(args):
     import torch
 
@@ -502,6 +527,7 @@ def run_ours(args):
 
     batched = None if args.no_batched else _bench_batched(sp2, sp2_inputs, dev)
     network = None if args.no_network else _bench_network(sp2, sp2_inputs, dev)
+    fermi = None if args.no_network else _bench_fermi(sp2, sp2_inputs, dev)
 
     # Gershgorin, input layer and its row norms, then one squaring launch per layer slot
     launches_per_step = 3 + st.launches
@@ -539,6 +565,7 @@ def run_ours(args):
         "accelerated": accel,
         "batched": batched,
         "network": network,
+        "fermi_expansion": fermi,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": int(launches_per_step * args.steps),
@@ -560,6 +587,8 @@ def run_only(args):
     sp2.init(0, precision="split")
     if args.only == "batched":
         out = _bench_batched(sp2, sp2_inputs, dev, reps=max(1, args.steps), count=args.batched_count)
+    elif args.only == "fermi":
+        out = _bench_fermi(sp2, sp2_inputs, dev, reps=max(1, args.steps))
     else:
         out = _bench_network(sp2, sp2_inputs, dev, reps=max(1, args.steps))
     print(json.dumps({"only": args.only, **out}))

@@ -208,6 +208,32 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
 sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float* coef, int ckpt_every,
                                 const float* ckpt, const float* G_out, double* dcoef, float* G_in);
 
+/*
+ * Finite-temperature Fermi-operator expansion (Sec. "Optimized SP2 Finite
+ * Temperature Fermi-Operator Expansion"): the generalised SP2 layers with a
+ * readout,
+ *   X_0 = (H - e_lo I)/(e_hi - e_lo),
+ *   X_n = theta[n-1][0] X_{n-1}^2 + theta[n-1][1] X_{n-1} + theta[n-1][2] I,
+ *   D   = I - sum_{i=0}^{L} c_i X_i,
+ * the matrix form of F~(eps) = 1 - sum_i c_i eps_i on the scaled energy
+ * eps = (E - e_lo)/(e_hi - e_lo) (fit theta and c so that F~ approximates the
+ * Fermi function, e.g. 1/(exp(beta (eps - 1/2)) + 1)).
+ *
+ *   H       [B, N, N] device, B instances (1 <= N <= 8192, B N^2 < 2^31).
+ *   L       layers, 1 <= L <= SP2_MAX_LAYERS.
+ *   theta   [L, 3] HOST, c [L + 1] HOST, FP64.
+ *   e_lo, e_hi  the energy window mapped to [0, 1]; both 0 selects each
+ *           instance's Gershgorin bounds.
+ *   D_out   [B, N, N] device output (also the iterate's storage).
+ *   bounds  [B, 2] device (e_lo, e_hi used per instance) or NULL.
+ * Tensor-core precisions only (split or fp16; UNSUPPORTED otherwise).
+ * Stream-ordered; synchronises only to read Gershgorin bounds back.
+ * Errors: INVALID_ARG, NONFINITE / DEGENERATE_SPECTRUM (Gershgorin mode),
+ * UNSUPPORTED, CUDA, OOM.
+ */
+sp2_status sp2_fermi_expansion(const float* H, int B, int N, int L, const double* theta, const double* c,
+                               double e_lo, double e_hi, float* D_out, double* bounds);
+
 /* ---- single steps of the path, exposed for testing and composition ---- */
 
 /* Gershgorin spectral bounds (Alg. 1 inputs): bounds_out (HOST double[2]) =

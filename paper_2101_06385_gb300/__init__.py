@@ -153,6 +153,7 @@ def _load():
         "sp2_density_matrix_batched": (_I, [_P, _P, _P, _I, _D, _I, _P, _P]),
         "sp2_network_forward": (_I, [_P, _I, _I, _I, _P, _I, _P, _P, _P]),
         "sp2_network_backward": (_I, [_P, _I, _I, _I, _P, _I, _P, _P, _P, _P]),
+        "sp2_fermi_expansion": (_I, [_P, _I, _I, _I, _P, _P, _D, _D, _P, _P]),
         "sp2_gershgorin": (_I, [_P, _I, _P]),
         "sp2_split": (_I, [_P, _I, _I, _P, _P]),
         "sp2_layer": (_I, [_P, _I, _I, _F, _F, _F, _P, _P]),
@@ -342,6 +343,29 @@ def density_matrix_batched(Hs: Sequence[torch.Tensor], n_occ: Sequence[int], tol
     status = lib.sp2_density_matrix_batched(hp, ns, no, B, float(tol), int(max_iter), dp, st if sync else None)
     _check(status, allow=(0, 1))
     return Ds, (_stats_many(st, B) if sync else None)
+
+
+def fermi_expansion(H: torch.Tensor, theta, c, window: Optional[Tuple[float, float]] = None,
+                    out: Optional[torch.Tensor] = None) -> Tuple[torch.Tensor, torch.Tensor]:
+    """Finite-temperature expansion D = I - sum_i c_i X_i with
+    X_0 = (H - e_lo I)/(e_hi - e_lo) and X_n = a X^2 + b X + c I per layer
+    (theta [L, 3], c [L + 1]).  H is [N, N] or [B, N, N]; window (e_lo, e_hi)
+    or None for each instance's Gershgorin bounds.  Returns (D, bounds [B, 2])."""
+    _dev_f32(H, "H")
+    _ensure_init(H)
+    Hb = H if H.dim() == 3 else H.unsqueeze(0)
+    B, N = Hb.shape[0], Hb.shape[-1]
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1, 3))
+    cc = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1))
+    if cc.shape[0] != th.shape[0] + 1:
+        raise ValueError("c needs one more entry than theta has layers")
+    D = out if out is not None else torch.empty_like(Hb)
+    _dev_f32(D, "out")
+    bounds = torch.empty((B, 2), dtype=torch.float64, device=H.device)
+    lo, hi = (0.0, 0.0) if window is None else (float(window[0]), float(window[1]))
+    _check(_load().sp2_fermi_expansion(Hb.data_ptr(), B, N, th.shape[0], th.ctypes.data, cc.ctypes.data, lo, hi,
+                                       D.data_ptr(), bounds.data_ptr()))
+    return (D if H.dim() == 3 else D[0]), bounds
 
 
 def gershgorin(H: torch.Tensor) -> Tuple[float, float]:

@@ -63,7 +63,7 @@ enum BufId {
   B_HI0, B_LO0, B_HI1, B_LO1, B_Y0, B_Y1, B_CTL, B_TILES, B_TOFF, B_TCNT, B_TPART, B_IDONE,
   B_PART, B_TICKET, B_ERR, B_DPTR, B_NS, B_HS, B_TRACES, B_PARAMS, B_BOUNDS, B_RN, B_PART2,
   B_G, B_SEG, B_GH0, B_GL0, B_GH1, B_GL1, B_DOTS, B_TDOTS, B_PARAMS2, B_NALPHA, B_HP0, B_HP1, B_RNP0, B_RNP1,
-  B_COUNT
+  B_READOUT, B_RDIAG, B_COUNT
 };
 
 struct Buf {
@@ -1570,6 +1570,195 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
     dcoef[3 * n] = da;
     dcoef[3 * n + 1] = db;
     dcoef[3 * n + 2] = dc;
+  }
+  return SP2_OK;
+}
+
+// Finite-temperature expansion (Sec. "Optimized SP2 Finite Temperature
+// Fermi-Operator Expansion"): X_0 = (H - e_lo I)/(e_hi - e_lo),
+// X_{n+1} = a_n X_n^2 + b_n X_n + c_n I, D = I - sum_i c_i X_i.  The layers
+// run on the CTA-pair squaring kernel with the readout accumulated in the
+// epilogue; X_0 is the reflection I - S_0 of the SP2 input layer, folded into
+// the first layer's coefficients and the readout's start.
+sp2_status sp2_fermi_expansion(const float* H, int B, int N, int L, const double* theta, const double* c,
+                               double e_lo, double e_hi, float* D_out, double* bounds) {
+  t_err.clear();
+  CKS(require_init());
+  const bool fixed = (e_lo != 0.0 || e_hi != 0.0);
+  bool finite = theta && c;
+  for (int i = 0; finite && i < 3 * L; ++i) finite = std::isfinite(theta[i]);
+  for (int i = 0; finite && i <= L; ++i) finite = std::isfinite(c[i]);
+  if (!H || !D_out || H == D_out || B < 1 || B > 4096 || N < 1 || N > 8192 || (long long)B * N * N >= (1LL << 31) ||
+      L < 1 || L > SP2_MAX_LAYERS || !finite || (fixed && !(std::isfinite(e_lo) && std::isfinite(e_hi) && e_lo < e_hi))) {
+    set_err("sp2_fermi_expansion: invalid argument");
+    return SP2_ERR_INVALID_ARG;
+  }
+  if (!tc_precision(g.precision)) {
+    set_err("sp2_fermi_expansion: needs a tensor-core precision (split or fp16)");
+    return SP2_ERR_UNSUPPORTED;
+  }
+  const bool split = g.precision == SP2_PREC_SPLIT_FP16;
+  cudaStream_t st = g.stream;
+  const long long slot = (long long)N * N;
+
+  // per-instance records; fixed bounds go straight into the control blocks
+  void *ctl, *ns, *hs, *dptr;
+  CKS(ws(B_CTL, (size_t)B * sizeof(Ctl), &ctl));
+  CKS(ws(B_NS, B * sizeof(int), &ns));
+  CKS(ws(B_HS, B * sizeof(float*), &hs));
+  CKS(ws(B_DPTR, B * sizeof(float*), &dptr));
+  const int ggrid = (int)std::min<long long>((N + 7) / 8, std::max((N + 63) / 64, 2 * g.num_sms / B + 1));
+  const int igrid = (int)std::min<long long>(N, std::max(1, 8 * g.num_sms / B + 1));
+  const int rgrid = (int)std::min<long long>((N + 7) / 8, std::max(1, 2 * g.num_sms / B + 1));
+  void *part, *tick, *err;
+  CKS(ws(B_PART, (size_t)B * std::max(ggrid, igrid) * sizeof(double2), &part));
+  CKS(ws(B_TICKET, std::max(64, B) * sizeof(unsigned), &tick, true));
+  CKS(ws(B_ERR, sizeof(int), &err, true));
+  {
+    void* h;
+    CKS(staging((size_t)B * sizeof(Ctl) + B * (sizeof(int) + 2 * sizeof(void*)) + 64, &h));
+    Ctl* hc = (Ctl*)h;
+    for (int b = 0; b < B; ++b) {
+      init_ctl(hc + b, N, N / 2, 0.0, 1);
+      if (fixed) {
+        hc[b].e_min = e_lo;
+        hc[b].e_max = e_hi;
+      }
+    }
+    int* hn = (int*)(hc + B);
+    const float** hh = (const float**)(hn + B + (B & 1));
+    float** hd = (float**)(hh + B);
+    for (int b = 0; b < B; ++b) {
+      hn[b] = N;
+      hh[b] = H + (size_t)b * slot;
+      hd[b] = D_out + (size_t)b * slot;
+    }
+    CK(cudaMemcpyAsync(ctl, hc, (size_t)B * sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ns, hn, B * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(hs, hh, B * sizeof(void*), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dptr, hd, B * sizeof(void*), cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(g.stage_done, st));
+  }
+  std::vector<double> lo_b(B, e_lo), hi_b(B, e_hi);
+  if (!fixed) {
+    CK(launch_gershgorin_batched((const float* const*)hs, (const int*)ns, (Ctl*)ctl, B, (double2*)part,
+                                 (unsigned*)tick, ggrid, st));
+    void* hb;
+    CKS(staging((size_t)B * 2 * sizeof(double) + (size_t)B * sizeof(int), &hb));
+    CK(cudaMemcpy2DAsync(hb, 2 * sizeof(double), (char*)ctl + offsetof(Ctl, e_min), sizeof(Ctl), 2 * sizeof(double),
+                         B, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpy2DAsync((char*)hb + (size_t)B * 2 * sizeof(double), sizeof(int), (char*)ctl + offsetof(Ctl, status),
+                         sizeof(Ctl), sizeof(int), B, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double* bd = (const double*)hb;
+    const int* bs = (const int*)((char*)hb + (size_t)B * 2 * sizeof(double));
+    for (int b = 0; b < B; ++b) {
+      if (bs[b] < 0) {
+        set_err("instance %d: %s", b, bs[b] == SP2_ERR_NONFINITE ? "non-finite spectral bounds" : "degenerate spectrum");
+        return (sp2_status)bs[b];
+      }
+      lo_b[b] = bd[2 * b];
+      hi_b[b] = bd[2 * b + 1];
+    }
+  }
+  if (bounds)
+    CK(cudaMemcpy2DAsync(bounds, 2 * sizeof(double), (char*)ctl + offsetof(Ctl, e_min), sizeof(Ctl),
+                         2 * sizeof(double), B, cudaMemcpyDeviceToDevice, st));
+
+  // FP64 plan on the host: the input layer stores S_0 = alpha_0 I + Y_0 with
+  // alpha_0 = e_hi/w and Y_0 = -H/w; X_0 = I - S_0 = (1 - alpha_0) I - Y_0.
+  std::vector<LayerParams> params((size_t)L * B);
+  std::vector<double> d0(B);
+  for (int b = 0; b < B; ++b) {
+    const double w = hi_b[b] - lo_b[b];
+    double al = 1.0 - hi_b[b] / w;  // identity part of X_0 (= -e_lo/w)
+    d0[b] = c[0] * al;               // R_0 = c_0 X_0 = -c_0 Y_0 + c_0 al I
+    for (int n = 0; n < L; ++n) {
+      const double a = theta[3 * n], bb = theta[3 * n + 1], cp = theta[3 * n + 2];
+      const double an = a * al * al + bb * al + cp;
+      LayerParams p;
+      memset(&p, 0, sizeof(p));
+      p.ca_d = (n == 0 ? -1.0 : 1.0) * (2.0 * a * al + bb);  // layer 0 reads Y_0 = -(X_0 - al I)
+      p.cb_d = a;
+      p.cc_d = 0.0;
+      p.ca = (float)p.ca_d;
+      p.cb = (float)p.cb_d;
+      p.active = 1;
+      p.out_mode = (n == L - 1) ? OUT_D : OUT_Y;
+      p.rc_d = c[n + 1];
+      p.rc = (float)c[n + 1];
+      p.alpha_new = an;
+      params[(size_t)n * B + b] = p;
+      al = an;
+    }
+  }
+
+  int ntiles = 0;
+  CKS(upload_tiles(N, B, 2, &ntiles));
+  void *prm, *dd, *R, *rn;
+  CKS(ws(B_PARAMS, params.size() * sizeof(LayerParams), &prm));
+  CKS(ws(B_RDIAG, (size_t)B * sizeof(double), &dd));
+  CKS(ws(B_READOUT, (size_t)B * slot * sizeof(float), &R));
+  CKS(ws(B_RN, (size_t)B * N * sizeof(double), &rn));
+  {
+    void* h;
+    CKS(staging(params.size() * sizeof(LayerParams) + (size_t)B * sizeof(double), &h));
+    memcpy(h, params.data(), params.size() * sizeof(LayerParams));
+    memcpy((char*)h + params.size() * sizeof(LayerParams), d0.data(), (size_t)B * sizeof(double));
+    CK(cudaMemcpyAsync(prm, h, params.size() * sizeof(LayerParams), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dd, (char*)h + params.size() * sizeof(LayerParams), (size_t)B * sizeof(double),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(g.stage_done, st));
+  }
+  const long long ld_h = round_up(N, 64), slot_h = ld_h * N;
+  void *hi[2], *lo[2], *hp[2];
+  CKS(planes_for(split, 0, (size_t)slot_h * B * 2, &hi[0], &lo[0], &hp[0]));
+  CKS(planes_for(split, 1, (size_t)slot_h * B * 2, &hi[1], &lo[1], &hp[1]));
+  CUtensorMap m[2][4];
+  CKS(tmaps4_for(split ? hp[0] : hi[0], lo[0], N, B, ld_h, slot_h, m[0], kTcBM));
+  CKS(tmaps4_for(split ? hp[1] : hi[1], lo[1], N, B, ld_h, slot_h, m[1], kTcBM));
+
+  SqArgs A;
+  memset(&A, 0, sizeof(A));
+  A.Dptr = (float* const*)dptr;
+  A.Ns = (const int*)ns;
+  A.tiles = (const uint32_t*)g.buf[B_TILES].p;
+  A.ntiles = ntiles;
+  A.tile_off = (const int*)g.buf[B_TOFF].p;
+  A.tile_cnt = (const int*)g.buf[B_TCNT].p;
+  A.lp_per_instance = 1;
+  A.tile_part = (double2*)g.buf[B_TPART].p;
+  A.inst_done = (unsigned*)g.buf[B_IDONE].p;
+  A.rn = (const double*)rn;
+  A.ld_rn = N;
+  A.lo_scale = std::ldexp(1.0f, g.lo_scale_exp);
+  A.lo_unscale = std::ldexp(1.0f, -g.lo_scale_exp);
+  A.err = (int*)err;
+  A.Yin = D_out;
+  A.Yout = D_out;
+  A.ld_y = N;
+  A.slot_y = slot;
+  A.ld_h = ld_h;
+  A.slot_h = slot_h;
+  A.R = (float*)R;
+  void* rnp[2];
+  CKS(rnp_for(N, B, A, rnp));
+
+  // S_0 (shifted form) into D_out and its planes, R_0 = c_0 X_0, row norms of Y_0
+  CK(launch_input_layer((const float* const*)hs, (const int*)ns, N, D_out, N, slot, (__half*)hi[0], (__half*)lo[0],
+                        (__half*)hp[0], ld_h, slot_h, N, (int)ld_h, A.lo_scale, (Ctl*)ctl, nullptr, (double2*)part,
+                        (unsigned*)tick, 1, 0, B, igrid, st));
+  CK(launch_readout_init(D_out, N, slot, N, B, (float)(-c[0]), (const double*)dd, (float*)R, igrid, st));
+  CK(launch_rownorm(D_out, N, slot, (const int*)ns, B, N, (double*)rn, N, nullptr, nullptr, nullptr, rgrid, st));
+  const int grid = std::min(ntiles, g.num_sms) & ~1;
+  for (int n = 0; n < L; ++n) {
+    const int cur = n & 1;
+    A.lp = (const LayerParams*)prm + (size_t)n * B;
+    A.hi_out = (__half*)hi[cur ^ 1];
+    A.lo_out = (__half*)lo[cur ^ 1];
+    A.hp_out = (__half*)hp[cur ^ 1];
+    rnp_step(A, rnp, n);
+    CK(launch_syrk_tc2(A, m[cur], split, grid, st));
   }
   return SP2_OK;
 }

@@ -38,6 +38,12 @@ struct LayerParams {
   double ca_d, cb_d;  // diagonal:      Y'_ii = ca_d Y_ii + cb_d P_ii + cc_d
   double cc_d;
   double alpha_out;   // OUT_D: D_ii = Y'_ii + alpha_out, D_ij = Y'_ij
+  // readout (finite-temperature expansion, launches with SqArgs::R set):
+  // R += rc X' with X' = alpha_new I + Y' (diagonal in FP64); OUT_D writes
+  // D = I - R instead of X'
+  float rc;
+  int pad;
+  double rc_d, alpha_new;
 };
 
 // Re-centring of the shift: while the spectrum of S is still clustered the
@@ -114,6 +120,10 @@ __device__ inline void set_branch(Ctl* c, int sigma, bool final_layer) {
   p.alpha_out = final_layer ? an : 0.0;
   p.active = 1;
   p.out_mode = final_layer ? OUT_D : OUT_Y;
+  p.rc = 0.f;
+  p.pad = 0;
+  p.rc_d = 0.0;
+  p.alpha_new = 0.0;
   c->next = p;
 }
 
@@ -146,6 +156,10 @@ __device__ inline void set_poly(Ctl* c, double a, double b, double cp, bool fina
   p.alpha_out = final_layer ? an : 0.0;
   p.active = 1;
   p.out_mode = final_layer ? OUT_D : OUT_Y;
+  p.rc = 0.f;
+  p.pad = 0;
+  p.rc_d = 0.0;
+  p.alpha_new = 0.0;
   c->next = p;
 }
 

@@ -99,7 +99,9 @@ __device__ __forceinline__ float column_sums_sq(const float (&y)[32], bool valid
 // ADJ (adjoint mode, a.aux set): the tile also accumulates, over its part
 // of the full symmetric matrices, tr Yin, <Yin, aux> and <P, aux> on the
 // old values, summed per instance into a.dots_out.
-template <bool SPLIT, bool ADJ = false>
+// RO (readout mode, a.R set): R += rc X' on the upper tiles, D = I - R in
+// the launch that writes D (finite-temperature expansion).
+template <bool SPLIT, bool ADJ = false, bool RO = false>
 __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_t tmem_base, uint64_t* tmem_full,
                                     uint64_t* tmem_empty, volatile int* abort_flag, Shared& sh, int ew, int q,
                                     int lane) {
@@ -235,9 +237,10 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       }
       // one FP64 update per row, outside the unrolled element loop
       float ydo = 0.f;
+      double yd = 0.0;
       if (dchunk) {
         const double pd = (a.rn || a.rnp_in) ? rn_r : (double)p_d;
-        const double yd = p.ca_d * (double)yold_d + p.cb_d * pd + p.cc_d;
+        yd = p.ca_d * (double)yold_d + p.cb_d * pd + p.cc_d;
         tr += yd;
         const float ydf = (float)yd;
         ydo = outD ? (float)(yd + p.alpha_out) : ydf;
@@ -250,6 +253,54 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       for (int j = 0; j < 32; ++j) sqf = fmaf(y[j], y[j], sqf);
       sq += (double)sqf;
       if (rnp && c0 < N) rnp[(long long)(c0 >> 5) * a.ld_rnp + r] = sqf;
+      if (RO) {
+        // readout R += rc X' over the upper tiles (R is symmetric; its lower
+        // half is only needed as D, written with the mirror below)
+        float* Rr = a.R + (long long)b * a.slot_y + (long long)r * ld + c0;
+        float rv[32];
+        if (full_chunk) {
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4) {
+            const float4 o = reinterpret_cast<const float4*>(Rr)[j4];
+            rv[4 * j4 + 0] = o.x;
+            rv[4 * j4 + 1] = o.y;
+            rv[4 * j4 + 2] = o.z;
+            rv[4 * j4 + 3] = o.w;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) rv[j] = (c0 + j < N) ? Rr[j] : 0.f;
+        }
+        double rd = 0.0;
+        if (dchunk) {
+          float rold = 0.f;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j == jd) rold = rv[j];
+          rd = (double)rold + p.rc_d * (yd + p.alpha_new);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) rv[j] = fmaf(p.rc, y[j], rv[j]);
+        if (dchunk) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j == jd) rv[j] = (float)rd;
+        }
+        if (outD) {
+          // D = I - R: the values the D stores (and the mirror) write
+#pragma unroll
+          for (int j = 0; j < 32; ++j) y[j] = (c0 + j < N) ? -rv[j] : 0.f;
+          ydo = (float)(1.0 - rd);
+        } else if (full_chunk) {
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4)
+            reinterpret_cast<float4*>(Rr)[j4] = make_float4(rv[4 * j4], rv[4 * j4 + 1], rv[4 * j4 + 2], rv[4 * j4 + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (c0 + j < N) Rr[j] = rv[j];
+        }
+      }
       if (outD) {
 #pragma unroll
         for (int j = 0; j < 32; ++j)

@@ -53,6 +53,7 @@ struct SqArgs {
   int fused_ctl;           // 1: the last tile of an instance runs its control step with
                            //    (tr Y', ||Y'||_F^2) from the tiles (no row-norm launch)
   int nseg;                // 1: P = Y Y (one operand); 2: P = A B^T + B A^T (second map set)
+  float* R;                // readout accumulator R = sum_i c_i X_i (layout of Y), or nullptr
   const float* const* Hobs; // [batch] N x N matrices A: the launch that writes D (OUT_D) also
                             // accumulates Tr[D A] per instance into dots_out[3 b] (or nullptr)
   const float* aux;        // adjoint mode: Y_n, same layout as Yin; dots <P, aux>, <Yin, aux>
@@ -81,6 +82,9 @@ cudaError_t launch_split(const float* X, long long n, float lo_scale, __half* hi
 cudaError_t launch_split_pad(const float* X, long long ld_x, long long slot_x, int N, int B, float lo_scale,
                              __half* hi, __half* lo, __half* hp, long long ld_h, long long slot_h, int grid,
                              cudaStream_t st);
+// R[b] = s Y[b] + d[b] I (diagonal in FP64): the readout of the input layer.
+cudaError_t launch_readout_init(const float* Y, long long ld_y, long long slot_y, int N, int B, float s,
+                                const double* d, float* R, int grid_x, cudaStream_t st);
 cudaError_t launch_materialize(const float* Y, long long ld_y, long long slot_y, int N, int B, const double* alpha,
                                float* out, long long ld_o, long long slot_o, int grid_x, cudaStream_t st);
 cudaError_t launch_observable(const float* D, const float* A, long long n, double* block_out, int grid,

@@ -507,6 +507,27 @@ __global__ void split_pad_kernel(const float* __restrict__ X, long long ld_x, lo
   }
 }
 
+// ---------------------------------------------------------------- readout
+// R[b] = s Y[b] + d[b] I over the N x N block of each slot (diagonal in
+// FP64): the input layer's term c_0 X_0 of the finite-temperature readout.
+__global__ void readout_init_kernel(const float* __restrict__ Y, long long ld_y, long long slot_y, int N, float s,
+                                    const double* __restrict__ d, float* __restrict__ R) {
+  const int b = blockIdx.y;
+  for (int r = blockIdx.x; r < N; r += gridDim.x) {
+    const float* yr = Y + (long long)b * slot_y + (long long)r * ld_y;
+    float* rr = R + (long long)b * slot_y + (long long)r * ld_y;
+    for (int c = threadIdx.x; c < N; c += blockDim.x)
+      rr[c] = (c == r) ? (float)((double)s * (double)yr[c] + d[b]) : s * yr[c];
+  }
+}
+
+cudaError_t launch_readout_init(const float* Y, long long ld_y, long long slot_y, int N, int B, float s,
+                                const double* d, float* R, int grid_x, cudaStream_t st) {
+  dim3 grid(grid_x, B);
+  readout_init_kernel<<<grid, 256, 0, st>>>(Y, ld_y, slot_y, N, s, d, R);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- materialise
 // out[b] = Y[b] + alpha[b] I (FP64 add on the diagonal, one rounding): the
 // full iterate X = alpha I + Y, e.g. for a network checkpoint.

@@ -81,7 +81,8 @@ __device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
                : "memory");
 }
 
-template <bool SPLIT>
+// RO: readout mode of the epilogue (finite-temperature expansion).
+template <bool SPLIT, bool RO>
 __global__ void __launch_bounds__(THREADS, 1)
     syrk_tc2_kernel(const __grid_constant__ CUtensorMap tm_p0A, const __grid_constant__ CUtensorMap tm_p1A,
                     const __grid_constant__ CUtensorMap tm_p0B, const __grid_constant__ CUtensorMap tm_p1B,
@@ -252,7 +253,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t it = 0;
     for (int u = cl; u < nsuper; u += ncl) {
       const int t = 2 * u + rank;
-      const int rc = epi::tile<SPLIT>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag, s_epi, ew, q, lane);
+      const int rc = epi::tile<SPLIT, false, RO>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag, s_epi, ew, q,
+                                                  lane);
       if (rc < 0) break;
       it += (uint32_t)rc;
     }
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 namespace {
 template <typename K>
 cudaError_t set_smem_once(K kernel, int bytes, int which) {
-  static int done_dev[2] = {-1, -1};
+  static int done_dev[4] = {-1, -1, -1, -1};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -309,14 +311,24 @@ cudaError_t launch_syrk_tc2(const SqArgs& a, const CUtensorMap* tm, bool split, 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e;
-  if (split) {
-    e = set_smem_once(tc2::syrk_tc2_kernel<true>, (int)smem, 1);
+  if (a.R) {
+    if (split) {
+      e = set_smem_once(tc2::syrk_tc2_kernel<true, true>, (int)smem, 3);
+      if (e != cudaSuccess) return e;
+      e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<true, true>, tm[0], tm[1], tm[2], tm[3], a);
+    } else {
+      e = set_smem_once(tc2::syrk_tc2_kernel<false, true>, (int)smem, 2);
+      if (e != cudaSuccess) return e;
+      e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<false, true>, tm[0], tm[1], tm[2], tm[3], a);
+    }
+  } else if (split) {
+    e = set_smem_once(tc2::syrk_tc2_kernel<true, false>, (int)smem, 1);
     if (e != cudaSuccess) return e;
-    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<true>, tm[0], tm[1], tm[2], tm[3], a);
+    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<true, false>, tm[0], tm[1], tm[2], tm[3], a);
   } else {
-    e = set_smem_once(tc2::syrk_tc2_kernel<false>, (int)smem, 0);
+    e = set_smem_once(tc2::syrk_tc2_kernel<false, false>, (int)smem, 0);
     if (e != cudaSuccess) return e;
-    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<false>, tm[0], tm[1], tm[2], tm[3], a);
+    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<false, false>, tm[0], tm[1], tm[2], tm[3], a);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
