@@ -156,8 +156,22 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
   const uint32_t taddr = tmem_base + buf * BN + ((uint32_t)(q * 32) << 16) + hc * 128;
   const bool vec_y = (ld & 3) == 0;
 
+  // chunks wholly past the padded K extent (columns >= round_up(N, 64)) or
+  // warps whose 32 rows all lie past N have nothing to write (warp-uniform)
+  const int kpad = (N + 63) & ~63;
+  const bool rows_live = I * BN + h * BM + q * 32 < N;
+
 #pragma unroll 1
   for (int ch = 0; ch < 4; ++ch) {
+    const int c0 = J * BN + hc * 128 + ch * 32;
+    if (!rows_live || c0 >= kpad) {
+      if (ch == 3) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tmem_empty[buf]);
+      }
+      continue;
+    }
     uint32_t v[32];
     __syncwarp();
     tmem_ld32(taddr + ch * 32, v);
@@ -168,7 +182,6 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       __syncwarp();
       if (lane == 0) mbar_arrive(&tmem_empty[buf]);
     }
-    const int c0 = J * BN + hc * 128 + ch * 32;
     // the diagonal element of row r, if it lies in this chunk (I == J only)
     const int jd = r - c0;
     const bool dchunk = !mirror && (unsigned)jd < 32u;
@@ -255,51 +268,57 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       if (rnp && c0 < N) rnp[(long long)(c0 >> 5) * a.ld_rnp + r] = sqf;
       if (RO) {
         // readout R += rc X' over the upper tiles (R is symmetric; its lower
-        // half is only needed as D, written with the mirror below)
+        // half is only needed as D, written with the mirror below); two
+        // halves of 16 columns keep the register footprint down
         float* Rr = a.R + (long long)b * a.slot_y + (long long)r * ld + c0;
-        float rv[32];
-        if (full_chunk) {
-#pragma unroll
-          for (int j4 = 0; j4 < 8; ++j4) {
-            const float4 o = reinterpret_cast<const float4*>(Rr)[j4];
-            rv[4 * j4 + 0] = o.x;
-            rv[4 * j4 + 1] = o.y;
-            rv[4 * j4 + 2] = o.z;
-            rv[4 * j4 + 3] = o.w;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) rv[j] = (c0 + j < N) ? Rr[j] : 0.f;
-        }
         double rd = 0.0;
-        if (dchunk) {
-          float rold = 0.f;
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (j == jd) rold = rv[j];
-          rd = (double)rold + p.rc_d * (yd + p.alpha_new);
+        for (int hh = 0; hh < 2; ++hh) {
+          float rv[16];
+          if (full_chunk) {
+#pragma unroll
+            for (int j4 = 0; j4 < 4; ++j4) {
+              const float4 o = reinterpret_cast<const float4*>(Rr + 16 * hh)[j4];
+              rv[4 * j4 + 0] = o.x;
+              rv[4 * j4 + 1] = o.y;
+              rv[4 * j4 + 2] = o.z;
+              rv[4 * j4 + 3] = o.w;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) rv[j] = (c0 + 16 * hh + j < N) ? Rr[16 * hh + j] : 0.f;
+          }
+          const bool dhalf = dchunk && (jd >> 4) == hh;
+          if (dhalf) {
+            float rold = 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (16 * hh + j == jd) rold = rv[j];
+            rd = (double)rold + p.rc_d * (yd + p.alpha_new);
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) rv[j] = fmaf(p.rc, y[16 * hh + j], rv[j]);
+          if (dhalf) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (16 * hh + j == jd) rv[j] = (float)rd;
+          }
+          if (outD) {
+            // D = I - R: the values the D stores (and the mirror) write
+#pragma unroll
+            for (int j = 0; j < 16; ++j) y[16 * hh + j] = (c0 + 16 * hh + j < N) ? -rv[j] : 0.f;
+          } else if (full_chunk) {
+#pragma unroll
+            for (int j4 = 0; j4 < 4; ++j4)
+              reinterpret_cast<float4*>(Rr + 16 * hh)[j4] =
+                  make_float4(rv[4 * j4], rv[4 * j4 + 1], rv[4 * j4 + 2], rv[4 * j4 + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + 16 * hh + j < N) Rr[16 * hh + j] = rv[j];
+          }
         }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) rv[j] = fmaf(p.rc, y[j], rv[j]);
-        if (dchunk) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (j == jd) rv[j] = (float)rd;
-        }
-        if (outD) {
-          // D = I - R: the values the D stores (and the mirror) write
-#pragma unroll
-          for (int j = 0; j < 32; ++j) y[j] = (c0 + j < N) ? -rv[j] : 0.f;
-          ydo = (float)(1.0 - rd);
-        } else if (full_chunk) {
-#pragma unroll
-          for (int j4 = 0; j4 < 8; ++j4)
-            reinterpret_cast<float4*>(Rr)[j4] = make_float4(rv[4 * j4], rv[4 * j4 + 1], rv[4 * j4 + 2], rv[4 * j4 + 3]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (c0 + j < N) Rr[j] = rv[j];
-        }
+        if (outD) ydo = (float)(1.0 - rd);
       }
       if (outD) {
 #pragma unroll
