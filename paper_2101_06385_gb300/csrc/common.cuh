@@ -1,7 +1,7 @@
 // Shared device-side definitions of the SP2 library (sm_103a).
 //
 // The iterate of Alg. 1 is stored as S = alpha I + Y with an FP64 scalar
-// alpha kept on the device and Y in FP32 (plus its FP16 hi/lo split).  With
+// alpha kept on the device and Y in FP32 (plus its FP16 planes).  With
 // the shift disabled alpha stays 0 and Y = S.  Both branches of the SP2
 // layer (Eq. 10 / Alg. 1, W_n = sigma_n I, B_n = (I - W_n) S_{n-1}) and the
 // generalised layer of Eq. 16 map onto the same element-wise epilogue

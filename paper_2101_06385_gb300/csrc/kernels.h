@@ -14,7 +14,8 @@ namespace sp2 {
 //
 // Storage of instance b (0 <= b < batch) with size n_b = Ns[b]:
 //   Y      FP32 iterate, element (r, c) at Y + b*slot_y + r*ld_y + c
-//   hi/lo  FP16 split of Y (tensor-core path), b*slot_h + r*ld_h + c; the
+//   planes FP16 planes of Y (tensor-core path: hp = 2^s hi and lo' for the
+//          split product, hi for plain FP16), b*slot_h + r*ld_h + c; the
 //          region [n_b, ld) of every row and rows >= n_b stay zero
 //   Dptr   per-instance final outputs [n_b, n_b] (ld n_b), used by OUT_D
 // Tiles: tiles[t] packs (b, I, J, h); the tiles of one instance are

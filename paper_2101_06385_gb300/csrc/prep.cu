@@ -219,9 +219,10 @@ __global__ void __launch_bounds__(256) gershgorin_batched_kernel(const float* co
 
 // ---------------------------------------------------------------- K2
 // Input layer for one instance (b = blockIdx.y): y = (shift ? -h : (e_max d_ij - h)) / (e_max - e_min)
-// written as FP32 into Y (ld_y, slot_y) and as the FP16 split into hi/lo
-// (ld_h, slot_h; padding up to Npad zero-filled).  FP64 partials (tr Y,
-// ||Y||_F^2) and, when ctl_step, the first control step by the last block.
+// written as FP32 into Y (ld_y, slot_y) and as the FP16 planes of Eq. 12
+// (hi, lo' and/or hp = 2^s hi, whichever pointers are set; ld_h, slot_h;
+// padding up to rows_pad x cols_pad zero-filled).  FP64 partial of tr Y and,
+// when ctl_step, the shift of S_0 and tr Y_0 for the first control step.
 __global__ void __launch_bounds__(256) input_layer_kernel(const float* const* __restrict__ Hs,
                                                           const int* __restrict__ Ns, long long ld_in_fixed,
                                                           float* __restrict__ Y, long long ld_y, long long slot_y,
@@ -485,7 +486,8 @@ __global__ void split_kernel(const float* __restrict__ X, long long n, float lo_
 }
 
 // ---------------------------------------------------------------- split, padded
-// X [B][N][ld_x] FP32 -> hi/lo [B][N][ld_h] FP16 with the row tail [N, ld_h) zeroed.
+// X [B][N][ld_x] FP32 -> FP16 planes hi / lo' / hp (each when set) [B][N][ld_h]
+// with the row tail [N, ld_h) zeroed.
 __global__ void split_pad_kernel(const float* __restrict__ X, long long ld_x, long long slot_x, int N, int B,
                                  float lo_scale, __half* __restrict__ hi, __half* __restrict__ lo,
                                  __half* __restrict__ hp, long long ld_h, long long slot_h) {

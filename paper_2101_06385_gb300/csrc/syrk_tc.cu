@@ -2,6 +2,10 @@
 // tcgen05.mma with FP32 accumulators in tensor memory, operands staged in
 // shared memory by TMA, fused SP2 layer epilogue.
 //
+// The two-accumulator kernel on hi/lo planes; it serves the allocation-free
+// solve (noalloc.cu).  The other solves use the single-accumulator kernels
+// of syrk_tc1.cu / syrk_tc2.cu.
+//
 // Alg. 2 / Eq. 14: with Y ~ hi + 2^-s lo (Eq. 12, lo scaled by 2^s),
 //     P = Y^2 ~ hi hi + 2^-s (lo hi + hi lo)          (the lo lo term is dropped)
 // Y is symmetric, so tile (I, J) of P is  sum_k Y[I, k] Y[J, k]^T: both MMA
