@@ -89,3 +89,12 @@ def test_unsafe_and_invalid_estimates(sp2):
     # the library still works afterwards
     D, st = sp2.density_matrix(H, h.n_occ)
     assert st.status == 0
+
+
+@pytest.mark.parametrize("N,n_occ", [(7, 3), (65, 1), (130, 129)])
+def test_ragged_and_extreme_occupations(sp2, N, n_occ):
+    h = si.gapped_hamiltonian(N, n_occ, (-1.0, -0.1), (0.1, 1.0), seed=70 + N)
+    homo, lumo = _homo_lumo(h)
+    D, st = sp2.density_matrix_accelerated(torch.from_numpy(h.h32()).cuda(), n_occ, homo, lumo)
+    m = o.error_metrics(D.cpu().numpy().astype(np.float64), o.density_matrix_closed_form(h.Q, n_occ), n_occ)
+    assert st.status == 0 and m["max_abs"] <= 5e-5 and m["trace_err"] <= 1e-4

@@ -88,3 +88,17 @@ def test_invalid_arguments(sp2):
         assert e.value.status == -8
     finally:
         sp2.set_precision("split")
+
+
+@pytest.mark.parametrize("N", [1, 5, 130])
+def test_ragged_and_tiny_sizes(sp2, N):
+    """Sizes below one tile and not a multiple of 4 (scalar paths)."""
+    theta, c = _fit()
+    rng = np.random.default_rng(N)
+    A = rng.uniform(-1.0, 1.0, (N, N))
+    H64 = ((A + A.T) / 2).astype(np.float32).astype(np.float64)
+    H = torch.from_numpy(H64.astype(np.float32)).cuda()
+    D, bounds = sp2.fermi_expansion(H, theta, c)
+    lo, hi = bounds.cpu().numpy()[0]
+    want = o.fermi_expansion_matrix(H64, theta, c, (lo, hi))
+    assert np.max(np.abs(D.cpu().numpy() - want)) <= 1e-4

@@ -95,3 +95,14 @@ def test_autograd_function(sp2):
     XL = o.network_forward(X0, coef.detach().numpy().astype(np.float64))
     want, _ = o.network_adjoint(X0, coef.detach().numpy().astype(np.float64), 2.0 * (XL - target.cpu().numpy()) / 2)
     assert np.max(np.abs(coef.grad.numpy() - want)) <= 1e-3 * np.max(np.abs(want))
+
+
+def test_forward_ragged_size(sp2):
+    """N not a multiple of 4 (scalar load/store paths of the epilogue)."""
+    rng = np.random.default_rng(2)
+    hs = _instances(2, 257, 3100)
+    coef = _coef(hs, 5, rng, 0.02).astype(np.float32)
+    H = torch.from_numpy(np.stack([h.h32() for h in hs])).cuda()
+    X, ck, _ = sp2.network_forward(H, coef, ckpt_every=5)
+    XL = o.network_forward(_oracle_x0(hs), coef.astype(np.float64))
+    assert np.max(np.abs(X.cpu().numpy() - XL)) <= 1e-4
