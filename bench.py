@@ -185,6 +185,28 @@ def _traffic_from_profile(n):
     return float(t.group(1)) if kernel_source_hash() == m.group(1) else None
 
 
+def _oracle_one_core(n=4096, rows=256):
+    """The oracle's layer sample on one core: a child process whose BLAS and
+    OpenMP pools are pinned to one thread before numpy loads; a seeded dense
+    symmetric n x n matrix, ``rows`` rows of the product."""
+    code = (
+        "import json, time, numpy as np, oracle\n"
+        f"rng = np.random.default_rng(0); A = rng.uniform(-1, 1, ({n}, {n})); S = (A + A.T) / 2\n"
+        f"oracle.sp2_layer_sample(S, 64)\n"
+        f"t = time.perf_counter(); oracle.sp2_layer_sample(S, {rows}); dt = time.perf_counter() - t\n"
+        f"print(json.dumps({{'value': 2.0 * {rows} * {n} ** 2 / dt / 1e12, 'unit': 'TFLOP/s', "
+        f"'sample': 'one FP64 layer, {rows} of {n} rows', 'seconds': dt}}))\n")
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    env["PYTHONPATH"] = ROOT + os.pathsep + env.get("PYTHONPATH", "")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        return json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return None
+
+
 def _cpu_model():
     try:
         for line in open("/proc/cpuinfo"):
@@ -484,19 +506,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         oracle.sp2_layer_sample(S0, rows)
         dt = time.perf_counter() - t0
-        # the same oracle layer on one core, on a smaller block of rows
-        one_core = None
-        try:
-            from threadpoolctl import threadpool_limits
-
-            r1 = 256
-            with threadpool_limits(limits=1):
-                t1 = time.perf_counter()
-                oracle.sp2_layer_sample(S0, r1)
-                d1 = time.perf_counter() - t1
-            one_core = {"value": 2.0 * r1 * N * N / d1 / 1e12, "unit": "TFLOP/s", "rows": r1, "seconds": d1}
-        except ImportError:
-            pass
+        one_core = _oracle_one_core()
         cpu = {"value": 2.0 * rows * N * N / dt / 1e12, "unit": "TFLOP/s", "cores": _cpu_threads(),
                "kind": "oracle", "cpu_model": _cpu_model(), "one_core": one_core,
                "sample": f"one FP64 SP2 layer restricted to {rows} of {N} rows (S[:rows] @ S + update + trace), "
