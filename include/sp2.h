@@ -181,6 +181,17 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
                                       double tol, int max_iter, float* const* D_out, sp2_stats* stats);
 
 /*
+ * Batched form of sp2_density_matrix_accelerated: instance b uses the HOMO /
+ * LUMO estimates homo[b] < lumo[b] (HOST arrays of batch doubles); other
+ * arguments, statuses and conventions as sp2_density_matrix_batched, plus
+ * BAD_ESTIMATE for an instance whose Tr D misses N_occ by more than 1/2
+ * (checked when stats is non-NULL).
+ */
+sp2_status sp2_density_matrix_batched_accelerated(const float* const* H, const int* N, const int* N_occ,
+                                                  const double* homo, const double* lumo, int batch, double tol,
+                                                  int max_iter, float* const* D_out, sp2_stats* stats);
+
+/*
  * Differentiable network (Eq. 16 in matrix form), batched over B instances:
  *   X_0 = (e_max I - H)/(e_max - e_min)    (Gershgorin bounds per instance, Alg. 1 input layer)
  *   X_{n+1} = a_n X_n^2 + b_n X_n + c_n I,  n = 0 .. L-1,

@@ -151,6 +151,7 @@ def _load():
         "sp2_density_matrix": (_I, [_P, _I, _I, _D, _I, _P, ctypes.POINTER(_Stats)]),
         "sp2_density_matrix_accelerated": (_I, [_P, _I, _I, _D, _D, _D, _I, _P, ctypes.POINTER(_Stats)]),
         "sp2_density_matrix_batched": (_I, [_P, _P, _P, _I, _D, _I, _P, _P]),
+        "sp2_density_matrix_batched_accelerated": (_I, [_P, _P, _P, _P, _P, _I, _D, _I, _P, _P]),
         "sp2_network_forward": (_I, [_P, _I, _I, _I, _P, _I, _P, _P, _P]),
         "sp2_network_backward": (_I, [_P, _I, _I, _I, _P, _I, _P, _P, _P, _P]),
         "sp2_fermi_expansion": (_I, [_P, _I, _I, _I, _P, _P, _D, _D, _P, _P]),
@@ -313,10 +314,7 @@ def density_matrix_accelerated(H: torch.Tensor, n_occ: int, homo: float, lumo: f
     return D, (_stats(st, status) if sync else None)
 
 
-def density_matrix_batched(Hs: Sequence[torch.Tensor], n_occ: Sequence[int], tol: float = 0.0,
-                           max_iter: int = 100, outs: Optional[Sequence[torch.Tensor]] = None,
-                           sync: bool = True):
-    """Many independent SP2 problems of uneven size (grouped launches)."""
+def _batched(Hs, n_occ, tol, max_iter, outs, sync, homo=None, lumo=None):
     if len(Hs) == 0:
         return [], []
     for i, h in enumerate(Hs):
@@ -340,9 +338,31 @@ def density_matrix_batched(Hs: Sequence[torch.Tensor], n_occ: Sequence[int], tol
     ns = (ctypes.c_int * B)(*sizes)
     no = (ctypes.c_int * B)(*[int(x) for x in n_occ])
     st = (_Stats * B)()
-    status = lib.sp2_density_matrix_batched(hp, ns, no, B, float(tol), int(max_iter), dp, st if sync else None)
+    if homo is None:
+        status = lib.sp2_density_matrix_batched(hp, ns, no, B, float(tol), int(max_iter), dp, st if sync else None)
+    else:
+        ho = (ctypes.c_double * B)(*[float(x) for x in homo])
+        lu = (ctypes.c_double * B)(*[float(x) for x in lumo])
+        status = lib.sp2_density_matrix_batched_accelerated(hp, ns, no, ho, lu, B, float(tol), int(max_iter), dp,
+                                                            st if sync else None)
     _check(status, allow=(0, 1))
     return Ds, (_stats_many(st, B) if sync else None)
+
+
+def density_matrix_batched(Hs: Sequence[torch.Tensor], n_occ: Sequence[int], tol: float = 0.0,
+                           max_iter: int = 100, outs: Optional[Sequence[torch.Tensor]] = None,
+                           sync: bool = True):
+    """Many independent SP2 problems of uneven size (grouped launches)."""
+    return _batched(Hs, n_occ, tol, max_iter, outs, sync)
+
+
+def density_matrix_batched_accelerated(Hs: Sequence[torch.Tensor], n_occ: Sequence[int], homo: Sequence[float],
+                                       lumo: Sequence[float], tol: float = 0.0, max_iter: int = 100,
+                                       outs: Optional[Sequence[torch.Tensor]] = None, sync: bool = True):
+    """Batched accelerated layers, one HOMO/LUMO estimate pair per instance."""
+    if len(homo) != len(Hs) or len(lumo) != len(Hs):
+        raise ValueError("one homo and one lumo estimate per instance")
+    return _batched(Hs, n_occ, tol, max_iter, outs, sync, homo, lumo)
 
 
 def fermi_expansion(H: torch.Tensor, theta, c, window: Optional[Tuple[float, float]] = None,

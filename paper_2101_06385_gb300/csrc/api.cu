@@ -829,7 +829,11 @@ namespace {
 // on super-tile pairs, else single CTAs on 128 x 256 tiles), enqueued on the
 // library stream; arguments checked by the caller.
 sp2_status batched_once(const float* const* H, const int* N, const int* N_occ, int B, int Nmax, double tol,
-                        int max_iter, float* const* D_out, bool pairs) {
+                        int max_iter, float* const* D_out, bool pairs, const double* homo, const double* lumo) {
+  const bool accel = homo != nullptr;
+  // launches per solve: the loop plus the two of Eq. 15 (none after the
+  // accelerated layers)
+  const int nlaunch = accel ? max_iter : max_iter + 2;
   const int prec = g.precision;
   const bool tc = tc_precision(prec);
   const bool split = prec == SP2_PREC_SPLIT_FP16;
@@ -885,7 +889,15 @@ sp2_status batched_once(const float* const* H, const int* N, const int* N_occ, i
   CKS(staging(bytes, &h));
   uint8_t* hbuf = (uint8_t*)h;
   Ctl* hc = (Ctl*)hbuf;
-  for (int b = 0; b < B; ++b) init_ctl(hc + b, N[b], N_occ[b], tol, max_iter);
+  for (int b = 0; b < B; ++b) {
+    init_ctl(hc + b, N[b], N_occ[b], tol, max_iter);
+    if (accel) {
+      hc[b].accel = 1;
+      hc[b].acc_homo = homo[b];
+      hc[b].acc_lumo = lumo[b];
+      hc[b].tol = tol > 0.0 ? tol : 1e-9;
+    }
+  }
   const void** hh = (const void**)(hc + B);
   void** hd = (void**)(hh + B);
   uint32_t* ht = (uint32_t*)(hd + B);
@@ -981,7 +993,7 @@ sp2_status batched_once(const float* const* H, const int* N, const int* N_occ, i
                         (double2*)part, (unsigned*)tick, rgrid, st));
       const int grid = std::min(nt, g.num_sms) & (pairs ? ~1 : ~0);
       CK(cudaEventRecordWithFlags(g.lev[0], st, evf));
-      for (int k = 0; k < max_iter + 2; ++k) {
+      for (int k = 0; k < nlaunch; ++k) {
         const int cur = k & 1;
         A.hi_out = (__half*)hi[cur ^ 1];
         A.lo_out = (__half*)lo[cur ^ 1];
@@ -1001,7 +1013,7 @@ sp2_status batched_once(const float* const* H, const int* N, const int* N_occ, i
       CK(launch_rownorm((float*)Y[0], ld_y, slot_y, (const int*)ns, B, Nmax, (double*)rn, Nmax, (Ctl*)ctl,
                         (double2*)part, (unsigned*)tick, rgrid, st));
       CK(cudaEventRecordWithFlags(g.lev[0], st, evf));
-      for (int k = 0; k < max_iter + 2; ++k) {
+      for (int k = 0; k < nlaunch; ++k) {
         const int cur = k & 1;
         A.Yin = (float*)Y[cur];
         A.Yout = (float*)Y[cur ^ 1];
@@ -1020,7 +1032,7 @@ sp2_status batched_once(const float* const* H, const int* N, const int* N_occ, i
   // it (sizes, grids, workspace addresses, stream) is unchanged; the per-call
   // records (control blocks, pointers, tile list) were uploaded above.
   if (g.use_graphs) {
-    const uint64_t key[] = {(uint64_t)B, (uint64_t)Nmax, (uint64_t)nt, (uint64_t)max_iter, (uint64_t)prec, (uint64_t)pairs,
+    const uint64_t key[] = {(uint64_t)B, (uint64_t)Nmax, (uint64_t)nt, (uint64_t)nlaunch, (uint64_t)prec, (uint64_t)pairs,
                             (uint64_t)g.shift, (uint64_t)g.lo_scale_exp, (uint64_t)igrid, (uint64_t)rgrid,
                             (uint64_t)ggrid, (uint64_t)g.num_sms, (uint64_t)(uintptr_t)st,
                             (uint64_t)(uintptr_t)hs, (uint64_t)(uintptr_t)ns, (uint64_t)(uintptr_t)ctl,
@@ -1072,10 +1084,14 @@ uint64_t batch_signature(const int* N, int B) {
 
 }  // namespace
 
-sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const int* N_occ, int batch, double tol,
-                                      int max_iter, float* const* D_out, sp2_stats* stats) {
+namespace {
+
+sp2_status batched_impl(const float* const* H, const int* N, const int* N_occ, int batch, double tol, int max_iter,
+                        float* const* D_out, sp2_stats* stats, const double* homo, const double* lumo) {
   t_err.clear();
   CKS(require_init());
+  const bool accel = homo != nullptr;
+  const int nlaunch = accel ? max_iter : max_iter + 2;
   if (!H || !N || !N_occ || !D_out || batch < 1 || batch > 4096 || !(tol >= 0.0) || !std::isfinite(tol) ||
       max_iter < 1 || max_iter > SP2_MAX_LAYERS - 3) {
     set_err("sp2_density_matrix_batched: invalid argument");
@@ -1108,7 +1124,7 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
       float best = 0.f;
       int pick = 0;
       for (int cand = 0; cand < 2; ++cand) {
-        CKS(batched_once(H, N, N_occ, B, Nmax, tol, max_iter, D_out, cand != 0));
+        CKS(batched_once(H, N, N_occ, B, Nmax, tol, max_iter, D_out, cand != 0, homo, lumo));
         CK(cudaEventSynchronize(g.ev1));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, g.ev0, g.ev1));
@@ -1123,7 +1139,7 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
       solved = pick == 1;
     }
   }
-  if (!solved) CKS(batched_once(H, N, N_occ, B, Nmax, tol, max_iter, D_out, pairs));
+  if (!solved) CKS(batched_once(H, N, N_occ, B, Nmax, tol, max_iter, D_out, pairs, homo, lumo));
 
   if (!stats) return SP2_OK;
   void* ctl = g.buf[B_CTL].p;
@@ -1143,26 +1159,54 @@ sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const
   const int e = *(const int*)((char*)hb + (size_t)B * sizeof(Ctl));
   float pro = 0.f, lms[SP2_MAX_LAYERS], sms[SP2_MAX_LAYERS];
   CK(cudaEventElapsedTime(&pro, g.ev0, g.lev[0]));
-  for (int k = 0; k < max_iter + 2; ++k) {
+  for (int k = 0; k < nlaunch; ++k) {
     CK(cudaEventElapsedTime(&lms[k], g.lev[k], g.lev[k + 1]));
     CK(cudaEventElapsedTime(&sms[k], g.lev[k], g.lsq[k]));
   }
   sp2_status worst = SP2_OK;
   for (int b = 0; b < B; ++b) {
     fill_stats(cs[b], &stats[b], ms, prec);
-    stats[b].launches = max_iter + 2;
+    stats[b].launches = nlaunch;
     if (tc) stats[b].energy = ((const double*)((const char*)hb + eoff))[3 * b];
     stats[b].prologue_ms = pro;
-    for (int k = 0; k < max_iter + 2; ++k) {
+    for (int k = 0; k < nlaunch; ++k) {
       stats[b].layer_ms[k] = lms[k];
       stats[b].square_ms[k] = sms[k];
     }
-    const sp2_status sb = status_of(cs[b], e);
+    sp2_status sb = status_of(cs[b], e);
+    if (accel && sb >= 0 && std::fabs(cs[b].trace_final - (double)N_occ[b]) > 0.5) {
+      set_err("instance %d: Tr D = %.3f but N_occ = %d; the HOMO/LUMO estimates do not bracket the gap", b,
+              cs[b].trace_final, N_occ[b]);
+      sb = SP2_ERR_BAD_ESTIMATE;
+    }
     if (sb < 0 && worst >= 0) worst = sb;
     if (sb == SP2_NOT_CONVERGED && worst == SP2_OK) worst = SP2_NOT_CONVERGED;
   }
   if (worst == SP2_OK) t_err.clear();
   return worst;
+}
+
+}  // namespace
+
+sp2_status sp2_density_matrix_batched(const float* const* H, const int* N, const int* N_occ, int batch, double tol,
+                                      int max_iter, float* const* D_out, sp2_stats* stats) {
+  return batched_impl(H, N, N_occ, batch, tol, max_iter, D_out, stats, nullptr, nullptr);
+}
+
+sp2_status sp2_density_matrix_batched_accelerated(const float* const* H, const int* N, const int* N_occ,
+                                                  const double* homo, const double* lumo, int batch, double tol,
+                                                  int max_iter, float* const* D_out, sp2_stats* stats) {
+  t_err.clear();
+  if (!homo || !lumo || batch < 1 || batch > 4096) {
+    set_err("sp2_density_matrix_batched_accelerated: invalid argument");
+    return SP2_ERR_INVALID_ARG;
+  }
+  for (int b = 0; b < batch; ++b)
+    if (!std::isfinite(homo[b]) || !std::isfinite(lumo[b]) || !(homo[b] < lumo[b])) {
+      set_err("sp2_density_matrix_batched_accelerated: invalid estimates for instance %d", b);
+      return SP2_ERR_INVALID_ARG;
+    }
+  return batched_impl(H, N, N_occ, batch, tol, max_iter, D_out, stats, homo, lumo);
 }
 
 // Host-side FP64 shift sequence of the network: X_n = alpha_n I + Y_n with

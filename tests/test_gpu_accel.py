@@ -98,3 +98,29 @@ def test_ragged_and_extreme_occupations(sp2, N, n_occ):
     D, st = sp2.density_matrix_accelerated(torch.from_numpy(h.h32()).cuda(), n_occ, homo, lumo)
     m = o.error_metrics(D.cpu().numpy().astype(np.float64), o.density_matrix_closed_form(h.Q, n_occ), n_occ)
     assert st.status == 0 and m["max_abs"] <= 5e-5 and m["trace_err"] <= 1e-4
+
+
+def test_batched_accelerated(sp2):
+    sizes = [300, 64, 777, 5, 1000]
+    hs = [si.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), seed=810 + i) for i, N in enumerate(sizes)]
+    Hs = [torch.from_numpy(h.h32()).cuda() for h in hs]
+    hl = [_homo_lumo(h) for h in hs]
+    Ds, stats = sp2.density_matrix_batched_accelerated(Hs, [h.n_occ for h in hs], [x[0] for x in hl],
+                                                       [x[1] for x in hl])
+    for h, D, st, (homo, lumo) in zip(hs, Ds, stats, hl):
+        m = o.error_metrics(D.cpu().numpy().astype(np.float64), o.density_matrix_closed_form(h.Q, h.n_occ), h.n_occ)
+        assert st.status == 0 and st.converged_by == "bounds"
+        assert m["max_abs"] <= 5e-5 and m["trace_err"] <= 1e-4
+        # the same layer sequence as solving the instance alone
+        _, s1 = sp2.density_matrix_accelerated(torch.from_numpy(h.h32()).cuda(), h.n_occ, homo, lumo)
+        assert s1.sigmas == st.sigmas
+        assert abs(st.energy - float(np.sum(np.sort(h.eps)[: h.n_occ]))) <= 1e-5 * np.sum(np.abs(h.eps))
+    # an unsafe estimate in one instance is reported
+    bad = [x[1] for x in hl]
+    occ1 = np.sort(hs[1].eps[: hs[1].n_occ])
+    homo_bad = [x[0] for x in hl]
+    homo_bad[1] = float(occ1[-8])
+    bad[1] = 0.9
+    with pytest.raises(sp2.SP2Error) as e:
+        sp2.density_matrix_batched_accelerated(Hs, [h.n_occ for h in hs], homo_bad, bad)
+    assert e.value.status == -9
