@@ -106,3 +106,27 @@ def test_forward_ragged_size(sp2):
     X, ck, _ = sp2.network_forward(H, coef, ckpt_every=5)
     XL = o.network_forward(_oracle_x0(hs), coef.astype(np.float64))
     assert np.max(np.abs(X.cpu().numpy() - XL)) <= 1e-4
+
+
+def test_training_steps_reduce_the_loss(sp2):
+    """The paper's learning of layer coefficients (Sec. "Capitalizing on the
+    machine learning perspective"): gradient steps through the hand-written
+    adjoint lower the Frobenius loss against the Fermi-Dirac target (C14, C16)."""
+    rng = np.random.default_rng(11)
+    hs = _instances(3, 256, 5200)
+    L = 8
+    coef0 = _coef(hs, L, rng, 0.03)
+    coef = torch.tensor(coef0, dtype=torch.float32, requires_grad=True)
+    H = torch.from_numpy(np.stack([h.h32() for h in hs])).cuda()
+    target = torch.from_numpy(np.stack([o.fermi_dirac_closed_form(h.Q, h.eps, 0.0, 0.05) for h in hs])).float().cuda()
+    opt = torch.optim.Adam([coef], lr=2e-3)
+    losses = []
+    for _ in range(12):
+        opt.zero_grad()
+        X = sp2.SP2Network.apply(H, coef, 2)
+        loss = ((X - target) ** 2).sum() / len(hs)
+        loss.backward()
+        opt.step()
+        losses.append(loss.item())
+    print("losses:", [round(v, 4) for v in losses])
+    assert losses[-1] < 0.8 * losses[0]
