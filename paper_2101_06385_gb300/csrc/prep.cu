@@ -15,8 +15,10 @@
 namespace sp2 {
 
 // ---------------------------------------------------------------- K1
-// One warp per row: R_i = sum_j |H_ij| - |H_ii|.  Float4 groups are summed
-// in FP32 (two additions) and accumulated in FP64.  Per-block min/max, then
+// One warp per row: R_i = sum_j |H_ij| - |H_ii|.  Groups of sixteen are
+// summed in FP32 as a four-level tree (relative error <= 4 x 2^-24) and
+// accumulated in FP64 (GB300's FP64 rate, not memory, would otherwise bound
+// the pass).  Per-block min/max, then
 // the last block folds all blocks and writes the bounds into each
 // instance's control block (or bounds_out).
 __global__ void __launch_bounds__(256) gershgorin_kernel(const float* __restrict__ H, int N, long long ld,
@@ -43,8 +45,11 @@ __global__ void __launch_bounds__(256) gershgorin_kernel(const float* __restrict
         float4 v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) v[u] = __ldcs(r4 + j + 32 * u);
+        float g4[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) a4[u] += (double)((fabsf(v[u].x) + fabsf(v[u].y)) + (fabsf(v[u].z) + fabsf(v[u].w)));
+        for (int u = 0; u < 4; ++u) g4[u] = (fabsf(v[u].x) + fabsf(v[u].y)) + (fabsf(v[u].z) + fabsf(v[u].w));
+        // the four groups in FP32 (a four-level tree of 16 terms), then FP64
+        a4[1] += (double)((g4[0] + g4[1]) + (g4[2] + g4[3]));
       }
       for (; j < n4; j += 32) {
         const float4 v = __ldcs(r4 + j);
@@ -286,19 +291,22 @@ __global__ void __launch_bounds__(256) input_layer_kernel(const float* const* __
               for (int u = 0; u < 4; ++u) hv[u] = (c4 + u < N) ? hrow[c4 + u] : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int col = c4 + u;
-              if (col < N) {
-                if (col == r) {
-                  const double v = -(double)hv[u] * inv + diag_add;
-                  y[u] = (float)v;
-                  tr += (double)y[u];
-                } else {
-                  y[u] = fmaf(-hv[u], inv_hi, -hv[u] * inv_lo);
-                }
-                sqf = fmaf(y[u], y[u], sqf);
-              }
+            for (int u = 0; u < 4; ++u) y[u] = (c4 + u < N) ? fmaf(-hv[u], inv_hi, -hv[u] * inv_lo) : 0.f;
+            // the diagonal element (at most one per group) in FP64, once
+            const int du = r - c4;
+            if ((unsigned)du < 4u) {
+              float hd = 0.f;
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (u == du) hd = hv[u];
+              const float yd = (float)(-(double)hd * inv + diag_add);
+              tr += (double)yd;
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (u == du) y[u] = yd;
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sqf = fmaf(y[u], y[u], sqf);
             if (c4 + 3 < N) {
               *reinterpret_cast<float4*>(yrow + c4) = make_float4(y[0], y[1], y[2], y[3]);
             } else {
