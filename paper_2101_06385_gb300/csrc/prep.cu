@@ -155,9 +155,11 @@ __global__ void __launch_bounds__(256) gershgorin_batched_kernel(const float* co
           const int j = j0 + u * 32 + lane;
           v[u] = (j < n4) ? __ldcs(r4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        float g4[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          acc += (double)((fabsf(v[u].x) + fabsf(v[u].y)) + (fabsf(v[u].z) + fabsf(v[u].w)));
+        for (int u = 0; u < 4; ++u) g4[u] = (fabsf(v[u].x) + fabsf(v[u].y)) + (fabsf(v[u].z) + fabsf(v[u].w));
+        // sixteen terms as an FP32 tree, one FP64 add (as the single-matrix kernel)
+        acc += (double)((g4[0] + g4[1]) + (g4[2] + g4[3]));
       }
     } else {
       for (int j = lane; j < N; j += 32) acc += (double)fabsf(row[j]);
