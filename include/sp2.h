@@ -5,9 +5,13 @@
  * Finkelstein et al., "Mixed Precision Fermi-Operator Expansion on Tensor
  * Cores From a Machine Learning Perspective" (arXiv:2101.06385):
  *   Alg. 1  (layer loop, branch choice, parameter-free convergence),
- *   Alg. 2 / Eqs. 12-14 (split FP16 hi/lo squaring with FP32 accumulation),
+ *   Alg. 2 / Eqs. 12-14 (split FP16 squaring with FP32 accumulation; the
+ *            pair is stored as hp = 2^s hi and lo' = 2^s lo),
  *   Eq. 15  (refinement layer f_final),
- *   Eq. 16  (generalised second-order layer, used by the network entry points).
+ *   Eq. 16  (generalised second-order layer, used by the network entry points),
+ *   Sec. "Accelerated Deep-NN SP2" (bound-driven layers from HOMO/LUMO estimates),
+ *   Sec. "Optimized SP2 Finite Temperature Fermi-Operator Expansion"
+ *            (generalised layers with a readout).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -82,7 +86,8 @@ typedef struct {
 } sp2_config;
 
 typedef struct {
-  int iterations;                 /* n: squaring layers of the loop (refinement not counted) */
+  int iterations;                 /* n: squaring layers of the loop (refinement not counted;
+                                     the accelerated solves count all their layers) */
   int converged_by;               /* sp2_stop_reason */
   int status_device;              /* sp2_status recorded on the device */
   int n_occ;
@@ -92,9 +97,11 @@ typedef struct {
   double alpha;                   /* identity shift of the last iterate (0 without shift) */
   double time_ms;                 /* device time of the whole call (CUDA events) */
   double flops_alg;               /* algorithmic FLOPs: layers x 3N^3 (split), N^3 (fp16/fp32) */
-  double prologue_ms;             /* device time of the bounds + input layer kernels */
-  int launches;                   /* squaring launches enqueued (max_iter + 2); launches past
-                                     iterations + 2 find the solve finished and return at once */
+  double prologue_ms;             /* device time of the bounds, input layer and first row-norm
+                                     kernels */
+  int launches;                   /* squaring launches enqueued (max_iter + 2; max_iter for the
+                                     accelerated solves); launches past the last layer find the
+                                     solve finished and return at once */
   int8_t sigma[SP2_MAX_LAYERS];   /* sigma[k] = sigma_{k+1} in {+1,-1}; 0 past the end */
   double iderr[SP2_MAX_LAYERS];   /* iderr[k] = IdErr_{k+1} */
   float layer_ms[SP2_MAX_LAYERS]; /* device time of layer k (k < launches): the loop layers, then
