@@ -172,6 +172,29 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       }
       continue;
     }
+    // the diagonal element of row r, if it lies in this chunk (I == J only)
+    const int jd = r - c0;
+    const bool dchunk = !mirror && (unsigned)jd < 32u;
+    const bool full_chunk = (c0 + 32 <= N) && vec_y;
+    // old values first: their global-load latency overlaps the TMEM load
+    float y[32];
+    if (r >= N) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) y[j] = 0.f;
+    } else if (full_chunk) {
+      const float4* src = reinterpret_cast<const float4*>(Yold + (long long)r * ld + c0);
+#pragma unroll
+      for (int j4 = 0; j4 < 8; ++j4) {
+        const float4 o = src[j4];
+        y[4 * j4 + 0] = o.x;
+        y[4 * j4 + 1] = o.y;
+        y[4 * j4 + 2] = o.z;
+        y[4 * j4 + 3] = o.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) y[j] = (c0 + j < N) ? Yold[(long long)r * ld + c0 + j] : 0.f;
+    }
     uint32_t v[32];
     __syncwarp();
     tmem_ld32(taddr + ch * 32, v);
@@ -182,29 +205,7 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       __syncwarp();
       if (lane == 0) mbar_arrive(&tmem_empty[buf]);
     }
-    // the diagonal element of row r, if it lies in this chunk (I == J only)
-    const int jd = r - c0;
-    const bool dchunk = !mirror && (unsigned)jd < 32u;
-    float y[32];
-    if (r >= N) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) y[j] = 0.f;
-    } else {
-      const bool full_chunk = (c0 + 32 <= N) && vec_y;
-      if (full_chunk) {
-        const float4* src = reinterpret_cast<const float4*>(Yold + (long long)r * ld + c0);
-#pragma unroll
-        for (int j4 = 0; j4 < 8; ++j4) {
-          const float4 o = src[j4];
-          y[4 * j4 + 0] = o.x;
-          y[4 * j4 + 1] = o.y;
-          y[4 * j4 + 2] = o.z;
-          y[4 * j4 + 3] = o.w;
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) y[j] = (c0 + j < N) ? Yold[(long long)r * ld + c0 + j] : 0.f;
-      }
+    if (r < N) {
       float yold_d = 0.f, p_d = 0.f;
       if (dchunk) {
 #pragma unroll
