@@ -723,6 +723,7 @@ sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int
     void* rnp[2];
     CKS(rnp_for(N, 1, A, rnp));
     A.fused_ctl = 1;
+    A.tri_y = 1;  // between launches only the upper triangle of Y' is kept
     CK(cudaEventRecord(g.lev[0], st));
     for (int k = 0; k < nlaunch; ++k) {
       const int cur = k & 1;
@@ -965,6 +966,7 @@ sp2_status batched_once(const float* const* H, const int* N, const int* N_occ, i
     A.ld_h = ld_h;
     A.slot_h = slot_h;
     A.fused_ctl = 1;
+    A.tri_y = 1;  // between launches only the upper triangle of Y' is kept
   } else {
     CKS(ws(B_Y1, (size_t)slot_y * B * 4, &Y[1]));
   }
@@ -1785,6 +1787,7 @@ sp2_status sp2_fermi_expansion(const float* H, int B, int N, int L, const double
   A.ld_h = ld_h;
   A.slot_h = slot_h;
   A.R = (float*)R;
+  A.tri_y = 1;  // between launches only the upper triangle of Y' is kept
   void* rnp[2];
   CKS(rnp_for(N, B, A, rnp));
 

@@ -5,8 +5,9 @@
 // with the diagonal in FP64 from the row norms (Y^2)_ii = sum_k Y_ik^2,
 // re-split Y' into the FP16 operand planes of the next layer (Eq. 12: hp =
 // 2^s hi and lo' for the split kernels, hi for plain FP16), store the
-// upper tile and its mirror, and publish the tile's FP64 (tr Y', ||Y'||_F^2)
-// partial.
+// upper tile and its mirror (of Y' itself only the upper tile when the
+// launch keeps the iterate as a triangle, SqArgs::tri_y), and publish the
+// tile's FP64 (tr Y', ||Y'||_F^2) partial.
 //
 // Warp ew (0..7) owns TMEM lane quarter q (the warp's index mod 4, a
 // hardware rule) and column half ew / 4: 32 rows x 128 columns, drained in
@@ -148,6 +149,8 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
   __half* ho = a.hi_out ? a.hi_out + (long long)b * a.slot_h : nullptr;
   __half* lo_ = a.lo_out ? a.lo_out + (long long)b * a.slot_h : nullptr;
   __half* hp_ = a.hp_out ? a.hp_out + (long long)b * a.slot_h : nullptr;
+  // the plane scaled like the accumulator's operands: hp for split, hi for plain
+  __half* const pa_out = SPLIT ? hp_ : ho;
   const long long ldh = a.ld_h;
   float* D = outD ? a.Dptr[b] : nullptr;
   double tr = 0.0, sq = 0.0;
@@ -196,6 +199,7 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       for (int j = 0; j < 32; ++j) y[j] = (c0 + j < N) ? Yold[(long long)r * ld + c0 + j] : 0.f;
     }
     uint32_t v[32];
+    const bool packs = !outD && r < N && (pa_out || lo_) && c0 + 32 <= (int)ldh;
     __syncwarp();
     tmem_ld32(taddr + ch * 32, v);
     tmem_ld_wait();
@@ -361,37 +365,6 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
           for (int j = 0; j < 32; ++j)
             if (c0 + j < N) Y[(long long)r * ld + c0 + j] = y[j];
         }
-        if ((ho || lo_ || hp_) && c0 + 32 <= (int)ldh) {
-          // 32 halves per plane, packed in registers; columns >= N carry zeros
-          uint32_t ph[16], pl[16], pp[16];
-#pragma unroll
-          for (int j2 = 0; j2 < 16; ++j2) {
-            __half h0, l0, h1, l1;
-            split_fp16(y[2 * j2], lo_scale, h0, l0);
-            split_fp16(y[2 * j2 + 1], lo_scale, h1, l1);
-            ph[j2] = pack_h2(h0, h1);
-            pl[j2] = pack_h2(l0, l1);
-            pp[j2] = pack_h2(__float2half_rn(__half2float(h0) * lo_scale), __float2half_rn(__half2float(h1) * lo_scale));
-          }
-          if (ho) {
-            uint4* dh = reinterpret_cast<uint4*>(ho + (long long)r * ldh + c0);
-#pragma unroll
-            for (int j4 = 0; j4 < 4; ++j4)
-              dh[j4] = make_uint4(ph[4 * j4], ph[4 * j4 + 1], ph[4 * j4 + 2], ph[4 * j4 + 3]);
-          }
-          if (lo_) {
-            uint4* dl = reinterpret_cast<uint4*>(lo_ + (long long)r * ldh + c0);
-#pragma unroll
-            for (int j4 = 0; j4 < 4; ++j4)
-              dl[j4] = make_uint4(pl[4 * j4], pl[4 * j4 + 1], pl[4 * j4 + 2], pl[4 * j4 + 3]);
-          }
-          if (hp_) {
-            uint4* dp = reinterpret_cast<uint4*>(hp_ + (long long)r * ldh + c0);
-#pragma unroll
-            for (int j4 = 0; j4 < 4; ++j4)
-              dp[j4] = make_uint4(pp[4 * j4], pp[4 * j4 + 1], pp[4 * j4 + 2], pp[4 * j4 + 3]);
-          }
-        }
       }
     }
     // row norms of the mirror: rows c0 + j of Y' get the segment of the 32
@@ -401,22 +374,51 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       if (c0 + lane < N) rnp[(long long)((I * BN + h * BM + q * 32) >> 5) * a.ld_rnp + c0 + lane] = cs;
     }
     // mirrored store: lanes hold consecutive rows r -> consecutive columns
-    if (mirror && r < N) {
+    if (mirror && r < N && (outD || !a.tri_y)) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int c = c0 + j;
         if (c < N) {
-          if (outD) {
+          if (outD)
             D[(long long)c * N + r] = y[j];
-          } else {
+          else
             Y[(long long)c * ld + r] = y[j];
-            if (ho || lo_ || hp_) {
-              __half hh, ll;
-              split_fp16(y[j], lo_scale, hh, ll);
-              if (ho) ho[(long long)c * ldh + r] = hh;
-              if (lo_) lo_[(long long)c * ldh + r] = ll;
-              if (hp_) hp_[(long long)c * ldh + r] = __float2half_rn(__half2float(hh) * lo_scale);
-            }
+        }
+      }
+    }
+    if (packs) {
+      // FP16 planes of Y': 32 halves per plane packed in registers, stored
+      // to the row segment and (off-diagonal tiles) its mirror; columns >= N
+      // carry zeros
+      uint32_t pa[16], pl[16];  // hp (split) or hi (plain), and lo'
+#pragma unroll
+      for (int j2 = 0; j2 < 16; ++j2) {
+        __half h0, l0, h1, l1;
+        split_fp16(y[2 * j2], lo_scale, h0, l0);
+        split_fp16(y[2 * j2 + 1], lo_scale, h1, l1);
+        pa[j2] = SPLIT ? pack_h2(__float2half_rn(__half2float(h0) * lo_scale),
+                                 __float2half_rn(__half2float(h1) * lo_scale))
+                       : pack_h2(h0, h1);
+        pl[j2] = pack_h2(l0, l1);
+      }
+      if (pa_out) {
+        uint4* dp = reinterpret_cast<uint4*>(pa_out + (long long)r * ldh + c0);
+#pragma unroll
+        for (int j4 = 0; j4 < 4; ++j4) dp[j4] = make_uint4(pa[4 * j4], pa[4 * j4 + 1], pa[4 * j4 + 2], pa[4 * j4 + 3]);
+      }
+      if (lo_) {
+        uint4* dl = reinterpret_cast<uint4*>(lo_ + (long long)r * ldh + c0);
+#pragma unroll
+        for (int j4 = 0; j4 < 4; ++j4) dl[j4] = make_uint4(pl[4 * j4], pl[4 * j4 + 1], pl[4 * j4 + 2], pl[4 * j4 + 3]);
+      }
+      if (mirror) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = c0 + j;
+          if (c < N) {
+            const int sh16 = 16 * (j & 1);
+            if (pa_out) pa_out[(long long)c * ldh + r] = __ushort_as_half((unsigned short)(pa[j >> 1] >> sh16));
+            if (lo_) lo_[(long long)c * ldh + r] = __ushort_as_half((unsigned short)(pl[j >> 1] >> sh16));
           }
         }
       }

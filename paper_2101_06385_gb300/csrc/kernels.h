@@ -26,7 +26,8 @@ struct SqArgs {
   long long ld_y, slot_y;
   __half* hi_out;          // FP16 planes of the updated iterate, each written when set:
   __half* lo_out;          //   hi = fp16(Y'), lo' = fp16(2^s (Y' - hi)),
-  __half* hp_out;          //   hp = 2^s hi (single-accumulator kernels)
+  __half* hp_out;          //   hp = 2^s hi (single-accumulator kernels: split writes hp_out
+                           //   and lo_out, plain FP16 hi_out and lo_out)
   long long ld_h, slot_h;
   float* const* Dptr;      // [batch] device array of output pointers (OUT_D)
   const int* Ns;           // [batch]
@@ -60,6 +61,10 @@ struct SqArgs {
   const float* aux;        // adjoint mode: Y_n, same layout as Yin; dots <P, aux>, <Yin, aux>
   double* tile_dots;       // [ntiles][3] per-tile (tr Yin, <Yin, aux>, <P, aux>) in adjoint mode
   double* dots_out;        // [batch][3] per-instance sums of tile_dots
+  int tri_y;               // 1: Y' is kept as its upper triangle: off-diagonal tiles skip the
+                           //    mirror store of Y' (the next launch reads the old values of
+                           //    the upper tiles only); the operand planes and the D of the
+                           //    final launch are stored whole
   float lo_scale;          // 2^s
   float lo_unscale;        // 2^-s
   int* err;                // device error word (SP2_ERR_DEVICE_TIMEOUT on a timed-out wait)
