@@ -498,23 +498,58 @@ __global__ void split_kernel(const float* __restrict__ X, long long n, float lo_
 // ---------------------------------------------------------------- split, padded
 // X [B][N][ld_x] FP32 -> FP16 planes hi / lo' / hp (each when set) [B][N][ld_h]
 // with the row tail [N, ld_h) zeroed.
+__device__ __forceinline__ uint32_t pack_half2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
 __global__ void split_pad_kernel(const float* __restrict__ X, long long ld_x, long long slot_x, int N, int B,
                                  float lo_scale, __half* __restrict__ hi, __half* __restrict__ lo,
                                  __half* __restrict__ hp, long long ld_h, long long slot_h) {
   const long long rows = (long long)N * B;
+  // four elements per thread: float4 loads, 8-byte stores per plane
+  const bool vec = ((ld_x | slot_x | ld_h | slot_h) & 3) == 0 && (((uintptr_t)X) & 15) == 0 &&
+                   ((((uintptr_t)hi) | ((uintptr_t)lo) | ((uintptr_t)hp)) & 7) == 0;
   for (long long gr = blockIdx.x; gr < rows; gr += gridDim.x) {
     const int b = (int)(gr / N), r = (int)(gr % N);
     const float* xr = X + (long long)b * slot_x + (long long)r * ld_x;
     __half* hr = hi ? hi + (long long)b * slot_h + (long long)r * ld_h : nullptr;
     __half* lr = lo ? lo + (long long)b * slot_h + (long long)r * ld_h : nullptr;
     __half* pr = hp ? hp + (long long)b * slot_h + (long long)r * ld_h : nullptr;
-    for (int c = threadIdx.x; c < (int)ld_h; c += blockDim.x) {
-      const float x = (c < N) ? xr[c] : 0.f;
-      __half h, l;
-      split_fp16(x, lo_scale, h, l);
-      if (hr) hr[c] = h;
-      if (lr) lr[c] = l;
-      if (pr) pr[c] = __float2half_rn(__half2float(h) * lo_scale);
+    if (vec) {
+      for (int c4 = threadIdx.x; c4 < (int)(ld_h >> 2); c4 += blockDim.x) {
+        const int c = c4 << 2;
+        float x[4];
+        if (c + 4 <= N) {
+          const float4 v = reinterpret_cast<const float4*>(xr)[c4];
+          x[0] = v.x;
+          x[1] = v.y;
+          x[2] = v.z;
+          x[3] = v.w;
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) x[u] = (c + u < N) ? xr[c + u] : 0.f;
+        }
+        __half h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) split_fp16(x[u], lo_scale, h[u], l[u]);
+        if (hr) *reinterpret_cast<uint2*>(hr + c) = make_uint2(pack_half2(h[0], h[1]), pack_half2(h[2], h[3]));
+        if (lr) *reinterpret_cast<uint2*>(lr + c) = make_uint2(pack_half2(l[0], l[1]), pack_half2(l[2], l[3]));
+        if (pr) {
+          __half q[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) q[u] = __float2half_rn(__half2float(h[u]) * lo_scale);
+          *reinterpret_cast<uint2*>(pr + c) = make_uint2(pack_half2(q[0], q[1]), pack_half2(q[2], q[3]));
+        }
+      }
+    } else {
+      for (int c = threadIdx.x; c < (int)ld_h; c += blockDim.x) {
+        const float x = (c < N) ? xr[c] : 0.f;
+        __half h, l;
+        split_fp16(x, lo_scale, h, l);
+        if (hr) hr[c] = h;
+        if (lr) lr[c] = l;
+        if (pr) pr[c] = __float2half_rn(__half2float(h) * lo_scale);
+      }
     }
   }
 }
@@ -522,14 +557,31 @@ __global__ void split_pad_kernel(const float* __restrict__ X, long long ld_x, lo
 // ---------------------------------------------------------------- readout
 // R[b] = s Y[b] + d[b] I over the N x N block of each slot (diagonal in
 // FP64): the input layer's term c_0 X_0 of the finite-temperature readout.
+// R must not alias Y (the diagonal is read back after the rows are written).
 __global__ void readout_init_kernel(const float* __restrict__ Y, long long ld_y, long long slot_y, int N, float s,
                                     const double* __restrict__ d, float* __restrict__ R) {
   const int b = blockIdx.y;
+  const float* Yb = Y + (long long)b * slot_y;
+  float* Rb = R + (long long)b * slot_y;
+  const bool vec = ((ld_y | slot_y | N) & 3) == 0 && ((((uintptr_t)Y) | ((uintptr_t)R)) & 15) == 0;
   for (int r = blockIdx.x; r < N; r += gridDim.x) {
-    const float* yr = Y + (long long)b * slot_y + (long long)r * ld_y;
-    float* rr = R + (long long)b * slot_y + (long long)r * ld_y;
-    for (int c = threadIdx.x; c < N; c += blockDim.x)
-      rr[c] = (c == r) ? (float)((double)s * (double)yr[c] + d[b]) : s * yr[c];
+    const float* yr = Yb + (long long)r * ld_y;
+    float* rr = Rb + (long long)r * ld_y;
+    if (vec) {
+      for (int c4 = threadIdx.x; c4 < (N >> 2); c4 += blockDim.x) {
+        const float4 v = reinterpret_cast<const float4*>(yr)[c4];
+        reinterpret_cast<float4*>(rr)[c4] = make_float4(s * v.x, s * v.y, s * v.z, s * v.w);
+      }
+    } else {
+      for (int c = threadIdx.x; c < N; c += blockDim.x) rr[c] = s * yr[c];
+    }
+  }
+  // the diagonal of this block's rows in FP64, after the row writes above
+  __syncthreads();
+  for (long long k = threadIdx.x;; k += blockDim.x) {
+    const long long r = blockIdx.x + k * gridDim.x;
+    if (r >= N) break;
+    Rb[r * ld_y + r] = (float)((double)s * (double)Yb[r * ld_y + r] + d[b]);
   }
 }
 
@@ -542,19 +594,33 @@ cudaError_t launch_readout_init(const float* Y, long long ld_y, long long slot_y
 
 // ---------------------------------------------------------------- materialise
 // out[b] = Y[b] + alpha[b] I (FP64 add on the diagonal, one rounding): the
-// full iterate X = alpha I + Y, e.g. for a network checkpoint.
+// full iterate X = alpha I + Y, e.g. for a network checkpoint.  Each block
+// copies its rows (float4 when the layout allows) and then sets their
+// diagonal: one FP64 operation per row, none per element.
 __global__ void materialize_kernel(const float* __restrict__ Y, long long ld_y, long long slot_y, int N,
                                    const double* __restrict__ alpha, float* __restrict__ out, long long ld_o,
                                    long long slot_o) {
   const int b = blockIdx.y;
-  const double a = alpha[b];
+  const float* Yb = Y + (long long)b * slot_y;
+  float* Ob = out + (long long)b * slot_o;
+  const bool vec = ((ld_y | slot_y | ld_o | slot_o | N) & 3) == 0 && ((((uintptr_t)Y) | ((uintptr_t)out)) & 15) == 0;
   for (int r = blockIdx.x; r < N; r += gridDim.x) {
-    const float* yr = Y + (long long)b * slot_y + (long long)r * ld_y;
-    float* orow = out + (long long)b * slot_o + (long long)r * ld_o;
-    for (int c = threadIdx.x; c < N; c += blockDim.x) {
-      const float y = yr[c];
-      orow[c] = (r == c) ? (float)((double)y + a) : y;
+    const float* yr = Yb + (long long)r * ld_y;
+    float* orow = Ob + (long long)r * ld_o;
+    if (vec) {
+      for (int c4 = threadIdx.x; c4 < (N >> 2); c4 += blockDim.x)
+        reinterpret_cast<float4*>(orow)[c4] = reinterpret_cast<const float4*>(yr)[c4];
+    } else {
+      for (int c = threadIdx.x; c < N; c += blockDim.x) orow[c] = yr[c];
     }
+  }
+  // the diagonal of this block's rows in FP64, after the row copies above
+  __syncthreads();
+  const double a = alpha[b];
+  for (long long k = threadIdx.x;; k += blockDim.x) {
+    const long long r = blockIdx.x + k * gridDim.x;
+    if (r >= N) break;
+    Ob[r * ld_o + r] = (float)((double)Yb[r * ld_y + r] + a);
   }
 }
 
