@@ -63,7 +63,7 @@ enum BufId {
   B_HI0, B_LO0, B_HI1, B_LO1, B_Y0, B_Y1, B_CTL, B_TILES, B_TOFF, B_TCNT, B_TPART, B_IDONE,
   B_PART, B_TICKET, B_ERR, B_DPTR, B_NS, B_HS, B_TRACES, B_PARAMS, B_BOUNDS, B_RN, B_PART2,
   B_G, B_SEG, B_GH0, B_GL0, B_GH1, B_GL1, B_DOTS, B_TDOTS, B_PARAMS2, B_NALPHA, B_HP0, B_HP1, B_RNP0, B_RNP1,
-  B_READOUT, B_RDIAG, B_COUNT
+  B_READOUT, B_RDIAG, B_SEGP, B_COUNT
 };
 
 struct Buf {
@@ -1483,23 +1483,24 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
   int ntiles = 0;
   CKS(upload_tiles(N, B, 1, &ntiles));
   const long long ld_h = round_up(N, 64), slot_h = ld_h * N;
-  void *params, *params2, *nal, *rn, *err, *seg, *yh, *yl = nullptr, *gh[2], *gl[2] = {nullptr, nullptr}, *dots,
-       *tdots;
+  void *params, *params2, *nal, *rn, *err, *seg, *segp, *gh[2], *gl[2] = {nullptr, nullptr}, *dots, *tdots;
   CKS(ws(B_PARAMS, plan.params.size() * sizeof(LayerParams), &params));
   CKS(ws(B_PARAMS2, bp.size() * sizeof(LayerParams), &params2));
   CKS(ws(B_NALPHA, nalpha.size() * sizeof(double), &nal));
   CKS(ws(B_RN, (size_t)B * N * sizeof(double), &rn));
   CKS(ws(B_ERR, sizeof(int), &err, true));
   CKS(ws(B_SEG, (size_t)ce * B * slot * 4, &seg));
-  void* yhp = nullptr;
-  CKS(ws(B_HI0, (size_t)slot_h * B * 2, &yh));
-  if (split) CKS(ws(B_HP0, (size_t)slot_h * B * 2, &yhp));
-  CKS(ws(B_GH0, (size_t)slot_h * B * 2, &gh[0]));
-  CKS(ws(B_GH1, (size_t)slot_h * B * 2, &gh[1]));
+  // operand planes of the ce iterates of a segment, kept from the
+  // recomputation for the adjoint layers: p0 = hp (split) or hi (plain) and
+  // p1 = lo' (split only)
+  const int nplanes = split ? 2 : 1;
+  const size_t plane_bytes = (size_t)slot_h * B * 2;
+  CKS(ws(B_SEGP, plane_bytes * nplanes * ce, &segp));
+  CKS(ws(B_GH0, plane_bytes, &gh[0]));
+  CKS(ws(B_GH1, plane_bytes, &gh[1]));
   if (split) {
-    CKS(ws(B_LO0, (size_t)slot_h * B * 2, &yl));
-    CKS(ws(B_GL0, (size_t)slot_h * B * 2, &gl[0]));
-    CKS(ws(B_GL1, (size_t)slot_h * B * 2, &gl[1]));
+    CKS(ws(B_GL0, plane_bytes, &gl[0]));
+    CKS(ws(B_GL1, plane_bytes, &gl[1]));
   }
   CKS(ws(B_DOTS, (size_t)L * B * 3 * sizeof(double), &dots, true));
   CKS(ws(B_TDOTS, (size_t)ntiles * 3 * sizeof(double), &tdots));
@@ -1516,9 +1517,13 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
   CK(cudaEventRecord(g.stage_done, st));
 
   // operand planes: Y_n and G as hp = 2^s hi and lo' (split) or hi (plain);
-  // the G planes live in gh (hp or hi) and gl (lo')
-  CUtensorMap mY4[4], mG4[2][4];
-  CKS(tmaps4_for(split ? yhp : yh, yl, N, B, ld_h, slot_h, mY4));
+  // the planes of Y_{n0 + k} are segp0(k) / segp1(k), those of G live in gh
+  // (hp or hi) and gl (lo')
+  auto segp0 = [&](int k) { return (__half*)((char*)segp + plane_bytes * nplanes * k); };
+  auto segp1 = [&](int k) { return split ? (__half*)((char*)segp + plane_bytes * (nplanes * k + 1)) : nullptr; };
+  std::vector<CUtensorMap> mY((size_t)ce * 4);
+  for (int k = 0; k < ce; ++k) CKS(tmaps4_for(segp0(k), segp1(k), N, B, ld_h, slot_h, &mY[(size_t)k * 4]));
+  CUtensorMap mG4[2][4];
   CKS(tmaps4_for(gh[0], gl[0], N, B, ld_h, slot_h, mG4[0]));
   CKS(tmaps4_for(gh[1], gl[1], N, B, ld_h, slot_h, mG4[1]));
   const float ls = std::ldexp(1.0f, g.lo_scale_exp);
@@ -1545,6 +1550,9 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
   const int rgrid = (int)std::min<long long>((N + 7) / 8, std::max(1, 2 * g.num_sms / B + 1));
   const int tgrid = std::min(ntiles, g.num_sms);
   auto segY = [&](int i) { return (float*)seg + (size_t)i * B * slot; };
+  void* rnp[2];
+  SqArgs R0 = A;  // row-norm carry of the recomputation (rnp_for sets its strides)
+  CKS(rnp_for(N, B, R0, rnp));
 
   CK(cudaMemcpyAsync(G, G_out, (size_t)B * slot * 4, cudaMemcpyDeviceToDevice, st));
   CK(launch_split_pad((float*)G, N, slot, N, B, ls, split ? nullptr : (__half*)gh[0], (__half*)gl[0],
@@ -1553,28 +1561,36 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
   const int nseg_layers = (L + ce - 1) / ce;
   for (int sgi = nseg_layers - 1; sgi >= 0; --sgi) {
     const int n0 = sgi * ce, n1 = std::min(n0 + ce, L);
-    // Y_{n0} = X_{n0} - alpha_{n0} I from the checkpoint, then recompute to Y_{n1-1}
+    // Y_{n0} = X_{n0} - alpha_{n0} I from the checkpoint and its planes, then
+    // recompute to Y_{n1-1}: each launch also writes the planes of its
+    // output and carries the row norms to the next (as in the forward pass)
     CK(launch_materialize(ckpt + (size_t)sgi * B * slot, N, slot, N, B, (const double*)nal + (size_t)n0 * B,
                           segY(0), N, slot, mgrid, st));
+    CK(launch_split_pad(segY(0), N, slot, N, B, ls, split ? nullptr : segp0(0), segp1(0), split ? segp0(0) : nullptr,
+                        ld_h, slot_h, sgrid, st));
+    if (n1 - n0 > 1)
+      CK(launch_rownorm(segY(0), N, slot, (const int*)ns, B, N, (double*)rn, N, nullptr, nullptr, nullptr, rgrid, st));
     for (int n = n0; n + 1 < n1; ++n) {
-      float* Yn = segY(n - n0);
-      CK(launch_rownorm(Yn, N, slot, (const int*)ns, B, N, (double*)rn, N, nullptr, nullptr, nullptr, rgrid, st));
-      CK(launch_split_pad(Yn, N, slot, N, B, ls, (__half*)yh, (__half*)yl, (__half*)yhp, ld_h, slot_h, sgrid, st));
-      SqArgs F = A;
-      F.Yin = Yn;
-      F.Yout = segY(n + 1 - n0);
+      const int k = n - n0;
+      SqArgs F = R0;
+      F.Yin = segY(k);
+      F.Yout = segY(k + 1);
+      F.hi_out = split ? nullptr : segp0(k + 1);
+      F.hp_out = split ? segp0(k + 1) : nullptr;
+      F.lo_out = segp1(k + 1);
       F.rn = (const double*)rn;
       F.ld_rn = N;
+      rnp_step(F, rnp, k);
       F.lp = (const LayerParams*)params + (size_t)n * B;
       F.nseg = 1;
-      CK(launch_syrk_tc1(F, mY4, split, tgrid, st));
+      CK(launch_syrk_tc1(F, &mY[(size_t)k * 4], split, tgrid, st));
     }
     for (int n = n1 - 1; n >= n0; --n) {
-      float* Yn = segY(n - n0);
-      CK(launch_split_pad(Yn, N, slot, N, B, ls, split ? nullptr : (__half*)yh, (__half*)yl,
-                          split ? (__half*)yhp : nullptr, ld_h, slot_h, sgrid, st));
+      const int k = n - n0;
+      float* Yn = segY(k);
+      const CUtensorMap* mYk = &mY[(size_t)k * 4];
       // segment 1: Y_n rows x G rows (Y G), segment 2: G rows x Y_n rows (G Y)
-      CUtensorMap m8[8] = {mY4[0], mY4[1], mG4[cur][2], mG4[cur][3], mG4[cur][0], mG4[cur][1], mY4[2], mY4[3]};
+      CUtensorMap m8[8] = {mYk[0], mYk[1], mG4[cur][2], mG4[cur][3], mG4[cur][0], mG4[cur][1], mYk[2], mYk[3]};
       SqArgs Bk = A;
       Bk.Yin = (float*)G;
       Bk.Yout = (float*)G;
