@@ -130,3 +130,31 @@ def test_training_steps_reduce_the_loss(sp2):
         losses.append(loss.item())
     print("losses:", [round(v, 4) for v in losses])
     assert losses[-1] < 0.8 * losses[0]
+
+
+def test_adjoint_plain_fp16(sp2):
+    """The adjoint on the plain-FP16 tensor-core path (one product per tile,
+    hi planes only), segments of uneven length (L = 7, ckpt_every = 3).
+    Rounding each operand to FP16 (unit roundoff 2^-11) perturbs every layer
+    of forward recomputation and adjoint by about 5e-4 relative, so the
+    gradients are held to 1e-2 relative instead of the split path's 1e-3."""
+    rng = np.random.default_rng(13)
+    hs = _instances(2, 300, 4100)
+    L, ce = 7, 3
+    coef = _coef(hs, L, rng, 0.05).astype(np.float32)
+    H = torch.from_numpy(np.stack([h.h32() for h in hs])).cuda()
+    sp2.set_precision("fp16")
+    try:
+        X, ck, _ = sp2.network_forward(H, coef, ckpt_every=ce)
+        target = np.stack([o.fermi_dirac_closed_form(h.Q, h.eps, 0.0, 0.05) for h in hs])
+        G_L = (2.0 * (X.cpu().numpy().astype(np.float64) - target) / len(hs)).astype(np.float32)
+        dcoef, G0 = sp2.network_backward(H, coef, ce, ck, torch.from_numpy(G_L).cuda())
+    finally:
+        sp2.set_precision("split")
+    X0 = _oracle_x0(hs)
+    want_d, want_G0 = o.network_adjoint(X0, coef.astype(np.float64), G_L.astype(np.float64))
+    rel = np.max(np.abs(dcoef.numpy() - want_d)) / np.max(np.abs(want_d))
+    g0 = np.max(np.abs(G0.cpu().numpy() - want_G0)) / np.max(np.abs(want_G0))
+    print(f"adjoint fp16: dcoef rel {rel:.2e}, G0 rel {g0:.2e}")
+    assert rel <= 1e-2
+    assert g0 <= 1e-2
