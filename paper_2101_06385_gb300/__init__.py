@@ -26,7 +26,10 @@ __all__ = [
     "finalize",
     "set_precision",
     "density_matrix",
+    "density_matrix_accelerated",
     "density_matrix_batched",
+    "density_matrix_batched_accelerated",
+    "fermi_expansion",
     "gershgorin",
     "split",
     "layer",
