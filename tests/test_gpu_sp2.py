@@ -110,9 +110,16 @@ def test_errors(sp2):
 
 
 def test_max_iter_reports_not_converged(sp2):
+    """A solve cut off at max_iter still returns f_final of its last iterate
+    (Eq. 15), written whole although the iterate is kept as its upper
+    triangle between the layers: it matches the oracle's five-layer result
+    and is symmetric."""
     h = si.gapped_hamiltonian(300, 150, seed=2)
     D, st = _solve(sp2, h, "split", max_iter=5)
     assert st.status == 1 and st.iterations == 5 and st.converged_by == "max_iter"
+    want = o.sp2(h.h32().astype(np.float64), h.n_occ, max_iter=5).D
+    assert np.max(np.abs(D - want)) <= 5e-5
+    assert np.max(np.abs(D - D.T)) <= 1e-6
 
 
 @pytest.mark.parametrize("N", [257, 1000])
