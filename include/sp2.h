@@ -222,6 +222,11 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
  *   G_in   [B, N, N] device output dLoss/dX_0, or NULL.
  * Per layer, with G = G_{n+1}:  G_n = a_n (X_n G + G X_n) + b_n G,
  *   dL/da_n = <G, X_n^2>, dL/db_n = <G, X_n>, dL/dc_n = tr G.
+ * Workspace: the ckpt_every iterates of one checkpoint segment are
+ * recomputed and kept in FP32 together with their FP16 operand planes
+ * (about ckpt_every * B * N^2 * 8 bytes on the split path, * 6 on plain FP16),
+ * plus the FP32 adjoint and its planes.  Errors: INVALID_ARG, UNSUPPORTED
+ * (FP32 precision), CUDA / OOM, DEVICE_TIMEOUT.
  */
 sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float* coef, int ckpt_every,
                                 const float* ckpt, const float* G_out, double* dcoef, float* G_in);
