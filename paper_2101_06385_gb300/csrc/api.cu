@@ -240,7 +240,9 @@ namespace {
 
 // Tensor maps {p0(A box), p1(A box), p0(B box), p1(B box)} for the
 // single-accumulator squaring kernels: p0 = hp = 2^s hi and p1 = lo' for the
-// split product, p0 = hi (p1 unused, null) for plain FP16.
+// split product, p0 = hi (p1 unused, null) for plain FP16.  For the CTA-pair
+// kernel (box_b = kTcBM) m holds six maps: also {p0, p1} with 64 x 64 boxes,
+// its transposed reads of the K blocks left of the diagonal.
 sp2_status tmaps4_for(const void* p0, const void* p1, int N, int B, long long ld_h, long long slot_h, CUtensorMap* m,
                       int box_b = kTcBN) {
   const void* p1_ = p1 ? p1 : p0;
@@ -248,6 +250,9 @@ sp2_status tmaps4_for(const void* p0, const void* p1, int N, int B, long long ld
             make_tmap_f16(&m[1], p1_, N, N, B, ld_h, slot_h, 64, kTcBM) &&
             make_tmap_f16(&m[2], p0, N, N, B, ld_h, slot_h, 64, box_b) &&
             make_tmap_f16(&m[3], p1_, N, N, B, ld_h, slot_h, 64, box_b);
+  if (ok && box_b == kTcBM)
+    ok = make_tmap_f16(&m[4], p0, N, N, B, ld_h, slot_h, 64, 64) &&
+         make_tmap_f16(&m[5], p1_, N, N, B, ld_h, slot_h, 64, 64);
   if (!ok) {
     set_err("cuTensorMapEncodeTiled failed (N=%d, ld=%lld)", N, ld_h);
     return SP2_ERR_CUDA;
@@ -707,7 +712,7 @@ sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int
     // FP64 row norms of Y_0 and the first control step (sigma_1, IdErr_1)
     CK(launch_rownorm(D_out, N, (long long)N * N, (const int*)ns, 1, N, (double*)rn, N, (Ctl*)ctl, (double2*)part,
                       (unsigned*)tick, rgrid, st));
-    CUtensorMap m[2][4];
+    CUtensorMap m[2][6];  // four maps, six for the CTA-pair kernel
     const int boxb = g.pair_kernel ? kTcBM : kTcBN;
     CKS(tmaps4_for(split ? hp[0] : hi[0], lo[0], N, 1, ld_h, slot_h, m[0], boxb));
     CKS(tmaps4_for(split ? hp[1] : hi[1], lo[1], N, 1, ld_h, slot_h, m[1], boxb));
@@ -724,6 +729,7 @@ sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int
     CKS(rnp_for(N, 1, A, rnp));
     A.fused_ctl = 1;
     A.tri_y = 1;  // between launches only the upper triangle of Y' is kept
+    A.tri_planes = g.pair_kernel ? 1 : 0;  // and of the planes, where the kernel reads them so
     CK(cudaEventRecord(g.lev[0], st));
     for (int k = 0; k < nlaunch; ++k) {
       const int cur = k & 1;
@@ -952,7 +958,7 @@ sp2_status batched_once(const float* const* H, const int* N, const int* N_occ, i
   void* Y[2] = {nullptr, nullptr};
   void *hi[2] = {nullptr, nullptr}, *lo[2] = {nullptr, nullptr}, *hp[2] = {nullptr, nullptr};
   void* rnp[2] = {nullptr, nullptr};
-  CUtensorMap m[2][4];
+  CUtensorMap m[2][6];  // four maps, six for the CTA-pair kernel
   CKS(ws(B_Y0, (size_t)slot_y * B * 4, &Y[0]));
   if (tc) {
     CKS(planes_for(split, 0, (size_t)slot_h * B * 2, &hi[0], &lo[0], &hp[0]));
@@ -967,6 +973,7 @@ sp2_status batched_once(const float* const* H, const int* N, const int* N_occ, i
     A.slot_h = slot_h;
     A.fused_ctl = 1;
     A.tri_y = 1;  // between launches only the upper triangle of Y' is kept
+    A.tri_planes = pairs ? 1 : 0;  // and of the planes, where the kernel reads them so
   } else {
     CKS(ws(B_Y1, (size_t)slot_y * B * 4, &Y[1]));
   }
@@ -1372,7 +1379,7 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
   void* Y[2] = {X_out, nullptr};
   void *hi[2] = {nullptr, nullptr}, *lo[2] = {nullptr, nullptr}, *hp[2] = {nullptr, nullptr};
   long long ld_h = 0, slot_h = 0;
-  CUtensorMap m[2][4];
+  CUtensorMap m[2][6];  // four maps, six for the CTA-pair kernel
   if (tc) {
     ld_h = round_up(N, 64);
     slot_h = ld_h * N;
@@ -1776,7 +1783,7 @@ sp2_status sp2_fermi_expansion(const float* H, int B, int N, int L, const double
   void *hi[2], *lo[2], *hp[2];
   CKS(planes_for(split, 0, (size_t)slot_h * B * 2, &hi[0], &lo[0], &hp[0]));
   CKS(planes_for(split, 1, (size_t)slot_h * B * 2, &hi[1], &lo[1], &hp[1]));
-  CUtensorMap m[2][4];
+  CUtensorMap m[2][6];  // four maps, six for the CTA-pair kernel
   CKS(tmaps4_for(split ? hp[0] : hi[0], lo[0], N, B, ld_h, slot_h, m[0], kTcBM));
   CKS(tmaps4_for(split ? hp[1] : hi[1], lo[1], N, B, ld_h, slot_h, m[1], kTcBM));
 
@@ -1803,7 +1810,8 @@ sp2_status sp2_fermi_expansion(const float* H, int B, int N, int L, const double
   A.ld_h = ld_h;
   A.slot_h = slot_h;
   A.R = (float*)R;
-  A.tri_y = 1;  // between launches only the upper triangle of Y' is kept
+  A.tri_y = 1;       // between launches only the upper triangle of Y' is kept
+  A.tri_planes = 1;  // and of the planes (the CTA-pair kernel)
   void* rnp[2];
   CKS(rnp_for(N, B, A, rnp));
 

@@ -5,9 +5,10 @@
 // with the diagonal in FP64 from the row norms (Y^2)_ii = sum_k Y_ik^2,
 // re-split Y' into the FP16 operand planes of the next layer (Eq. 12: hp =
 // 2^s hi and lo' for the split kernels, hi for plain FP16), store the
-// upper tile and its mirror (of Y' itself only the upper tile when the
-// launch keeps the iterate as a triangle, SqArgs::tri_y), and publish the
-// tile's FP64 (tr Y', ||Y'||_F^2) partial.
+// upper tile and its mirror (only the upper tile of Y' when the launch keeps
+// the iterate as a triangle, SqArgs::tri_y, and of the planes when it keeps
+// them so, SqArgs::tri_planes), and publish the tile's FP64 (tr Y',
+// ||Y'||_F^2) partial.
 //
 // Warp ew (0..7) owns TMEM lane quarter q (the warp's index mod 4, a
 // hardware rule) and column half ew / 4: 32 rows x 128 columns, drained in
@@ -411,7 +412,7 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
 #pragma unroll
         for (int j4 = 0; j4 < 4; ++j4) dl[j4] = make_uint4(pl[4 * j4], pl[4 * j4 + 1], pl[4 * j4 + 2], pl[4 * j4 + 3]);
       }
-      if (mirror) {
+      if (mirror && !a.tri_planes) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int c = c0 + j;

@@ -61,6 +61,9 @@ struct SqArgs {
   const float* aux;        // adjoint mode: Y_n, same layout as Yin; dots <P, aux>, <Yin, aux>
   double* tile_dots;       // [ntiles][3] per-tile (tr Yin, <Yin, aux>, <P, aux>) in adjoint mode
   double* dots_out;        // [batch][3] per-instance sums of tile_dots
+  int tri_planes;          // 1: the operand planes too are kept as upper super tiles (the
+                           //    mirror plane stores are skipped); only for the CTA-pair kernel,
+                           //    whose operand reads use the upper super tiles alone
   int tri_y;               // 1: Y' is kept as its upper triangle: off-diagonal tiles skip the
                            //    mirror store of Y' (the next launch reads the old values of
                            //    the upper tiles only); the operand planes and the D of the
@@ -113,7 +116,9 @@ cudaError_t launch_syrk_tc1(const SqArgs& a, const CUtensorMap* tmaps, bool spli
 size_t syrk_tc1_smem_bytes(bool split);
 // The same kernel run by CTA pairs (clusters of 2) that share the B operand by
 // TMA multicast: tiles come in (h = 0, h = 1) pairs of one super tile,
-// a.ntiles = 2 x super tiles, and the B maps have 128-row boxes.
+// a.ntiles = 2 x super tiles, and the B maps have 128-row boxes.  tmaps holds
+// six maps: the four above and {p0, p1} with 64 x 64 boxes, through which the
+// K blocks left of the diagonal are read transposed from the upper tiles.
 cudaError_t launch_syrk_tc2(const SqArgs& a, const CUtensorMap* tmaps, bool split, int grid, cudaStream_t st);
 size_t syrk_tc2_smem_bytes(bool split);
 

@@ -27,6 +27,14 @@
 //   warps 2..9  epilogue: TMEM lane quarter (warp % 4) x column half
 // Plain FP16 (split = false): hi hi only, 48 KB stages, 4 stages.
 // Every mbarrier wait is bounded; see syrk_tc.cu for the time-out path.
+//
+// Operand reads use only the upper super tiles of the planes: a 64-wide K
+// block that lies left of the diagonal (super column k < I for the A rows of
+// super row I, k < J for B) is read from the stored block (k, I) or (k, J)
+// transposed: two 64 x 64 TMA boxes per operand half and an MN-major shared-
+// memory descriptor, with the operand's major bit set in the instruction
+// descriptor for that K block.  So the planes need only be written for the
+// upper super tiles (SqArgs::tri_planes).
 #include <cuda.h>
 #include <cuda_fp16.h>
 
@@ -48,6 +56,8 @@ constexpr int EPI_WARPS = epi::WARPS;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;  // two 256-column accumulators
 
+// one 64 x 64 FP16 box of a transposed read
+constexpr int T_BOX = 64 * 64 * 2;
 // stage offsets (split): hpA, loA (A_BYTES each), hpB, loB (B_BYTES each)
 constexpr int OFF_HPA = 0, OFF_LOA = A_BYTES, OFF_HPB = 2 * A_BYTES, OFF_LOB = 2 * A_BYTES + B_BYTES;
 
@@ -82,10 +92,12 @@ __device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
 }
 
 // RO: readout mode of the epilogue (finite-temperature expansion).
+// tm_p0T / tm_p1T: the planes with 64 x 64 boxes (transposed reads).
 template <bool SPLIT, bool RO>
 __global__ void __launch_bounds__(THREADS, 1)
     syrk_tc2_kernel(const __grid_constant__ CUtensorMap tm_p0A, const __grid_constant__ CUtensorMap tm_p1A,
                     const __grid_constant__ CUtensorMap tm_p0B, const __grid_constant__ CUtensorMap tm_p1B,
+                    const __grid_constant__ CUtensorMap tm_p0T, const __grid_constant__ CUtensorMap tm_p1T,
                     const SqArgs a) {
   constexpr int STAGES = SPLIT ? STAGES_SPLIT : STAGES_PLAIN;
   constexpr int STAGE_BYTES = SPLIT ? STAGE_SPLIT : STAGE_PLAIN;
@@ -159,14 +171,35 @@ __global__ void __launch_bounds__(THREADS, 1)
           uint8_t* st = smem + stage * STAGE_BYTES;
           mbar_expect_tx(&full[stage], STAGE_BYTES);
           const int k0 = kb * BK;
-          if (SPLIT) {
-            tma_load_3d(st + OFF_HPA, &tm_p0A, k0, rowA, b, &full[stage]);
-            tma_load_3d(st + OFF_LOA, &tm_p1A, k0, rowA, b, &full[stage]);
-            tma_load_3d_mc(st + OFF_HPB + rank * (B_BYTES / 2), &tm_p0B, k0, rowB, b, &full[stage], 0x3);
-            tma_load_3d_mc(st + OFF_LOB + rank * (B_BYTES / 2), &tm_p1B, k0, rowB, b, &full[stage], 0x3);
+          const int ks = k0 / BN;  // super column of this K block
+          // A rows: K-major from (I, k) on or right of the diagonal, else
+          // the stored (k, I) transposed as two 64 x 64 boxes
+          uint8_t* a0 = st + (SPLIT ? OFF_HPA : 0);
+          if (ks >= I) {
+            tma_load_3d(a0, &tm_p0A, k0, rowA, b, &full[stage]);
+            if (SPLIT) tma_load_3d(st + OFF_LOA, &tm_p1A, k0, rowA, b, &full[stage]);
           } else {
-            tma_load_3d(st, &tm_p0A, k0, rowA, b, &full[stage]);
-            tma_load_3d_mc(st + A_BYTES + rank * (B_BYTES / 2), &tm_p0B, k0, rowB, b, &full[stage], 0x3);
+            tma_load_3d(a0, &tm_p0T, rowA, k0, b, &full[stage]);
+            tma_load_3d(a0 + T_BOX, &tm_p0T, rowA + 64, k0, b, &full[stage]);
+            if (SPLIT) {
+              tma_load_3d(st + OFF_LOA, &tm_p1T, rowA, k0, b, &full[stage]);
+              tma_load_3d(st + OFF_LOA + T_BOX, &tm_p1T, rowA + 64, k0, b, &full[stage]);
+            }
+          }
+          // this CTA's half of the B rows, multicast into both CTAs
+          uint8_t* b0 = st + (SPLIT ? OFF_HPB : A_BYTES) + rank * (B_BYTES / 2);
+          if (ks >= J) {
+            tma_load_3d_mc(b0, &tm_p0B, k0, rowB, b, &full[stage], 0x3);
+            if (SPLIT)
+              tma_load_3d_mc(st + OFF_LOB + rank * (B_BYTES / 2), &tm_p1B, k0, rowB, b, &full[stage], 0x3);
+          } else {
+            tma_load_3d_mc(b0, &tm_p0T, rowB, k0, b, &full[stage], 0x3);
+            tma_load_3d_mc(b0 + T_BOX, &tm_p0T, rowB + 64, k0, b, &full[stage], 0x3);
+            if (SPLIT) {
+              uint8_t* b1 = st + OFF_LOB + rank * (B_BYTES / 2);
+              tma_load_3d_mc(b1, &tm_p1T, rowB, k0, b, &full[stage], 0x3);
+              tma_load_3d_mc(b1 + T_BOX, &tm_p1T, rowB + 64, k0, b, &full[stage], 0x3);
+            }
           }
           ++armed[stage];
           if (++stage == STAGES) {
@@ -199,6 +232,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int N = a.Ns[b];
         const int nk = (N + BK - 1) / BK;
         const uint32_t buf = it & 1u;
+        (void)h;
         // the k-th use of a buffer waits for the epilogue's (k-1)-th release
         if (!mbar_wait(&tmem_empty[buf], ((it >> 1) & 1u) ^ 1u, abort_flag)) {
           ok = false;
@@ -213,18 +247,28 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           tc_fence_after();
           const uint32_t st = smem_u32(smem + stage * STAGE_BYTES);
+          // operands left of the diagonal arrived transposed (MN-major)
+          const int sc = kb * BK / BN;
+          const bool ta = sc < I, tb = sc < J;
+          const uint32_t idesc = IDESC | (ta ? IDESC_A_MN : 0u) | (tb ? IDESC_B_MN : 0u);
 #pragma unroll
           for (int ks = 0; ks < BK / UMMA_K; ++ks) {
-            const uint32_t koff = ks * UMMA_K * 2;
+            // K step ks: 32 B along a K-major row, or two 8-row K groups
+            const uint32_t oa = ta ? ks * 2048u : ks * UMMA_K * 2u;
+            const uint32_t ob = tb ? ks * 2048u : ks * UMMA_K * 2u;
             const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
             if (SPLIT) {
-              const uint64_t dhpA = make_desc_sw128(st + OFF_HPA + koff);
-              const uint64_t dhpB = make_desc_sw128(st + OFF_HPB + koff);
-              mma_f16(d, dhpA, dhpB, acc);                                       // hp hp
-              mma_f16(d, make_desc_sw128(st + OFF_LOA + koff), dhpB, 1u);        // lo' hp
-              mma_f16(d, dhpA, make_desc_sw128(st + OFF_LOB + koff), 1u);        // hp lo'
+              const uint64_t dhpA = ta ? make_desc_mn128(st + OFF_HPA + oa) : make_desc_sw128(st + OFF_HPA + oa);
+              const uint64_t dloA = ta ? make_desc_mn128(st + OFF_LOA + oa) : make_desc_sw128(st + OFF_LOA + oa);
+              const uint64_t dhpB = tb ? make_desc_mn128(st + OFF_HPB + ob) : make_desc_sw128(st + OFF_HPB + ob);
+              const uint64_t dloB = tb ? make_desc_mn128(st + OFF_LOB + ob) : make_desc_sw128(st + OFF_LOB + ob);
+              mma_f16_id(d, dhpA, dhpB, idesc, acc);  // hp hp
+              mma_f16_id(d, dloA, dhpB, idesc, 1u);   // lo' hp
+              mma_f16_id(d, dhpA, dloB, idesc, 1u);   // hp lo'
             } else {
-              mma_f16(d, make_desc_sw128(st + koff), make_desc_sw128(st + A_BYTES + koff), acc);
+              const uint64_t dA = ta ? make_desc_mn128(st + oa) : make_desc_sw128(st + oa);
+              const uint64_t dB = tb ? make_desc_mn128(st + A_BYTES + ob) : make_desc_sw128(st + A_BYTES + ob);
+              mma_f16_id(d, dA, dB, idesc, acc);
             }
           }
           mma_commit_mc(&empty[stage], 0x3);  // release the stage in both CTAs
@@ -315,20 +359,20 @@ cudaError_t launch_syrk_tc2(const SqArgs& a, const CUtensorMap* tm, bool split, 
     if (split) {
       e = set_smem_once(tc2::syrk_tc2_kernel<true, true>, (int)smem, 3);
       if (e != cudaSuccess) return e;
-      e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<true, true>, tm[0], tm[1], tm[2], tm[3], a);
+      e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<true, true>, tm[0], tm[1], tm[2], tm[3], tm[4], tm[5], a);
     } else {
       e = set_smem_once(tc2::syrk_tc2_kernel<false, true>, (int)smem, 2);
       if (e != cudaSuccess) return e;
-      e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<false, true>, tm[0], tm[1], tm[2], tm[3], a);
+      e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<false, true>, tm[0], tm[1], tm[2], tm[3], tm[4], tm[5], a);
     }
   } else if (split) {
     e = set_smem_once(tc2::syrk_tc2_kernel<true, false>, (int)smem, 1);
     if (e != cudaSuccess) return e;
-    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<true, false>, tm[0], tm[1], tm[2], tm[3], a);
+    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<true, false>, tm[0], tm[1], tm[2], tm[3], tm[4], tm[5], a);
   } else {
     e = set_smem_once(tc2::syrk_tc2_kernel<false, false>, (int)smem, 0);
     if (e != cudaSuccess) return e;
-    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<false, false>, tm[0], tm[1], tm[2], tm[3], a);
+    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<false, false>, tm[0], tm[1], tm[2], tm[3], tm[4], tm[5], a);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

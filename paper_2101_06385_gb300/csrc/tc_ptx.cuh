@@ -114,6 +114,36 @@ __device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// MN-major operand (the transpose of a stored block) with the 128-byte
+// swizzle, as TMA writes a box of 64 (M or N) x 64 (K) FP16: each K row holds
+// 64 M elements in 128 B, rows 128 B apart.
+//   leading byte offset: between 64-element M blocks (one box each, 8 KB)
+//   stride byte offset:  between 8-row K groups (1024 B)
+// A K = 16 step advances the start address by two K groups (2048 B).
+__device__ __forceinline__ uint64_t make_desc_mn128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(8192u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
+// Instruction-descriptor bits selecting MN-major A (bit 15) and B (bit 16).
+constexpr uint32_t IDESC_A_MN = 1u << 15;
+constexpr uint32_t IDESC_B_MN = 1u << 16;
+
+// tcgen05.mma with a run-time instruction descriptor.
+__device__ __forceinline__ void mma_f16_id(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
