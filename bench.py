@@ -57,6 +57,8 @@ def _args():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--gen-device", default="gpu", choices=["gpu", "cpu"],
+                    help="where the input generator runs its FP64 QR (cpu: for runs under a profiler)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-SP2 measurement")
     ap.add_argument("--no-network", action="store_true", help="skip the network forward/backward measurement")
@@ -393,7 +395,8 @@ def run_ours(args):
     w = _workload(args.n)
     N, n_occ = w["N"], w["n_occ"]
     t_gen = time.perf_counter()
-    h = sp2_inputs.gapped_hamiltonian(N, n_occ, w["occ"], w["virt"], w["seed"], device=str(dev))
+    gen_dev = str(dev) if args.gen_device == "gpu" else "cpu"
+    h = sp2_inputs.gapped_hamiltonian(N, n_occ, w["occ"], w["virt"], w["seed"], device=gen_dev)
     t_gen = time.perf_counter() - t_gen
     H32 = h.h32()
     H = torch.from_numpy(H32).to(dev)

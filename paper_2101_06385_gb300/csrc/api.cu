@@ -91,8 +91,8 @@ struct State {
   cudaEvent_t lsq[SP2_MAX_LAYERS] = {};      // after each squaring launch
   // cached tile list
   int tiles_key_N = -1, tiles_key_B = -1, tiles_key_kind = -1;
-  // squaring kernel of the single-matrix solve: CTA pairs sharing B through
-  // TMA multicast (default) or single CTAs (SP2_SQUARE_KERNEL=single)
+  // squaring kernel of the single-matrix solve: CTA pairs with one M = 256
+  // MMA per super tile (default) or single CTAs (SP2_SQUARE_KERNEL=single)
   bool pair_kernel = true;
   // the batched solve's launch sequence as an instantiated CUDA graph, and
   // what was baked into it (SP2_GRAPHS=0 enqueues the launches directly)

@@ -95,6 +95,15 @@ __device__ __forceinline__ float column_sums_sq(const float (&y)[32], bool valid
   return s[0];
 }
 
+// Release of accumulator buffer buf by one lane of an epilogue warp.
+template <bool PAIR>
+__device__ __forceinline__ void release(uint64_t* tmem_empty, uint32_t buf, uint32_t empty_cl) {
+  if (PAIR)
+    sp2::tc::mbar_arrive_cl(empty_cl + 8u * buf);
+  else
+    sp2::tc::mbar_arrive(&tmem_empty[buf]);
+}
+
 // Tile t with accumulator use `it` (buffer it & 1).  Returns 0 when the
 // tile's instance is inactive (nothing issued for it), 1 when done, -1 when
 // the accumulator wait failed.
@@ -103,10 +112,13 @@ __device__ __forceinline__ float column_sums_sq(const float (&y)[32], bool valid
 // old values, summed per instance into a.dots_out.
 // RO (readout mode, a.R set): R += rc X' on the upper tiles, D = I - R in
 // the launch that writes D (finite-temperature expansion).
-template <bool SPLIT, bool ADJ = false, bool RO = false>
+// PAIR (CTA-pair kernels): the accumulator was written by the pair's MMA
+// issuer in the even CTA, and the release of a buffer is an arrive on that
+// CTA's barrier, empty_cl + 8 x buffer (a shared::cluster address).
+template <bool SPLIT, bool ADJ = false, bool RO = false, bool PAIR = false>
 __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_t tmem_base, uint64_t* tmem_full,
                                     uint64_t* tmem_empty, volatile int* abort_flag, Shared& sh, int ew, int q,
-                                    int lane) {
+                                    int lane, uint32_t empty_cl = 0u) {
   using namespace sp2::tc;
   int b, I, J, h;
   unpack_tile(a.tiles[t], b, I, J, h);
@@ -138,7 +150,8 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
   }
 
   const uint32_t buf = it & 1u;
-  const bool got = __all_sync(0xffffffffu, mbar_wait(&tmem_full[buf], (it >> 1) & 1u, abort_flag));
+  const bool got = __all_sync(0xffffffffu, PAIR ? mbar_wait_cl(&tmem_full[buf], (it >> 1) & 1u, abort_flag)
+                                                : mbar_wait(&tmem_full[buf], (it >> 1) & 1u, abort_flag));
   if (!got) {
     if (lane == 0) atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
     *abort_flag = 1;
@@ -172,7 +185,7 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       if (ch == 3) {
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&tmem_empty[buf]);
+        if (lane == 0) release<PAIR>(tmem_empty, buf, empty_cl);
       }
       continue;
     }
@@ -208,7 +221,7 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       // accumulator drained: the MMA issuer may reuse this buffer
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&tmem_empty[buf]);
+      if (lane == 0) release<PAIR>(tmem_empty, buf, empty_cl);
     }
     if (r < N) {
       float yold_d = 0.f, p_d = 0.f;

@@ -114,9 +114,10 @@ cudaError_t launch_rownorm(const float* Y, long long ld_y, long long slot_y, con
 // pointers are set (hp_out and lo_out for split, hi_out for plain).
 cudaError_t launch_syrk_tc1(const SqArgs& a, const CUtensorMap* tmaps, bool split, int grid, cudaStream_t st);
 size_t syrk_tc1_smem_bytes(bool split);
-// The same kernel run by CTA pairs (clusters of 2) that share the B operand by
-// TMA multicast: tiles come in (h = 0, h = 1) pairs of one super tile,
-// a.ntiles = 2 x super tiles, and the B maps have 128-row boxes.  tmaps holds
+// The same product run by CTA pairs (clusters of 2) whose MMAs span both CTAs
+// (M = 256 per super tile, each CTA holding 128 rows of A and of B): tiles
+// come in (h = 0, h = 1) pairs of one super tile, a.ntiles = 2 x super tiles,
+// and the B maps have 128-row boxes.  tmaps holds
 // six maps: the four above and {p0, p1} with 64 x 64 boxes, through which the
 // K blocks left of the diagonal are read transposed from the upper tiles.
 cudaError_t launch_syrk_tc2(const SqArgs& a, const CUtensorMap* tmaps, bool split, int grid, cudaStream_t st);

@@ -1,40 +1,51 @@
-// Single-accumulator split-FP16 squaring on tcgen05 with a double-buffered
-// TMEM accumulator, run by CTA pairs that share the B operand through TMA
-// multicast (sm_103a).
+// Single-accumulator split-FP16 squaring on tcgen05 run by CTA pairs: one
+// M = 256 MMA (tcgen05 .cta_group::2) per K step covers a whole 256 x 256
+// upper super tile, with a double-buffered TMEM accumulator (sm_103a).
 //
-// The two 128-row halves (h = 0, 1) of an upper 256 x 256 super tile need the
-// same 256 B rows.  A cluster of two CTAs takes both halves of one super tile;
-// each CTA loads its own 128 A rows and one 128-row half of B, and the B half
-// is multicast into both CTAs' shared memory, so B is read from L2 once per
-// super tile instead of twice.  A stage may be refilled only when both CTAs'
-// MMAs have released it (the release is a multicast commit).
+// The two CTAs of a cluster take the two 128-row halves of one super tile
+// (I, J).  Each CTA loads, per 64-wide K stage, its own 128 A rows (rows
+// I*256 + 128 rank ...) and its own 128 of the 256 B rows (rows J*256 + 128
+// rank ...) into its own shared memory with plain TMA loads; the pair MMA,
+// issued by one thread of the even CTA, reads the A and B halves of both CTAs
+// and writes rows 0-127 of the tile into the even CTA's tensor memory and
+// rows 128-255 into the odd CTA's.  So a CTA's stage holds 128 A rows and 128
+// B rows (64 KB split, three stages), and the tensor core of each SM reads
+// 256 operand rows from shared memory per 128 x 256 x 16 product, against
+// 384 for a single-CTA 128 x 256 tile.  Nothing is multicast: the tensor maps
+// cover this GPU's own planes and each byte lands only in the CTA that loads
+// it.
+//
+// Synchronisation of a pair:
+//   full[s]       even CTA only: its producer arms it with the bytes of both
+//                 CTAs' loads; the odd CTA's loads complete on it remotely
+//   empty[s]      one per CTA: the MMA issuer's commit releases stage s in
+//                 both CTAs (one commit per barrier)
+//   tmem_full[b]  one per CTA: committed by the MMA issuer to both
+//   tmem_empty[b] even CTA only: the 16 epilogue warps of both CTAs arrive
+//                 once they have drained accumulator buffer b
+// Every wait is bounded; an abort is also stored into the peer's flag.
 //
 // Alg. 2 / Eq. 14 with both parts scaled by 2^s (Eq. 12: hi = fp16(Y),
 // lo' = fp16(2^s (Y - hi)); hp = 2^s hi is exact in FP16 for |Y| < 2^(15-s)):
 //     2^(2s) P = hp hp + lo' hp + hp lo',
-// so only two FP16 planes (hp, lo') are stored and loaded, and the three
-// products accumulate into ONE FP32 TMEM accumulator of 128 x 256 (256
-// columns).  Scaling by powers of two commutes with every rounding, so the
-// result equals that of the unscaled products hi hi + lo hi + hi lo.  Two such accumulators fit in the 512 TMEM
-// columns: while the epilogue warps drain tile t from one, the MMA issuer
-// fills the other with tile t+1, and the epilogue (FP32 update, re-split,
-// row and mirrored stores, traces) runs under the next tile's MMAs.
+// so only two FP16 planes are stored and loaded, and the three products
+// accumulate into one FP32 accumulator of 256 columns; scaling by powers of
+// two commutes with every rounding.  Two accumulators fill the 512 TMEM
+// columns: the epilogue of tile t runs under the MMAs of tile t+1.
 //
-// CTA = 10 warps, persistent over the upper-tile list (one CTA per SM):
-//   warp 0      TMA producer (one thread): hp, lo' of the 128 A rows and of
-//               the 256 B rows per 64-wide K stage (96 KB, 2 stages)
-//   warp 1      TMEM allocation + MMA issuer (one thread)
-//   warps 2..9  epilogue: TMEM lane quarter (warp % 4) x column half
-// Plain FP16 (split = false): hi hi only, 48 KB stages, 4 stages.
-// Every mbarrier wait is bounded; see syrk_tc.cu for the time-out path.
+// CTA = 10 warps, persistent over the super-tile list (one CTA per SM):
+//   warp 0      TMA producer (one thread)
+//   warp 1      TMEM allocation (both CTAs) + MMA issuer (even CTA, one thread)
+//   warps 2..9  epilogue of the CTA's 128 rows (csrc/epilogue.cuh)
+// Plain FP16 (split = false): hi hi only, 32 KB stages, 6 stages.
 //
 // Operand reads use only the upper super tiles of the planes: a 64-wide K
-// block that lies left of the diagonal (super column k < I for the A rows of
-// super row I, k < J for B) is read from the stored block (k, I) or (k, J)
-// transposed: two 64 x 64 TMA boxes per operand half and an MN-major shared-
-// memory descriptor, with the operand's major bit set in the instruction
-// descriptor for that K block.  So the planes need only be written for the
-// upper super tiles (SqArgs::tri_planes).
+// block left of the diagonal (super column k < I for the A rows of super row
+// I, k < J for B) is read from the stored block (k, I) or (k, J) transposed,
+// as two 64 x 64 TMA boxes per 128-row half and an MN-major shared-memory
+// descriptor, with the operand's major bit set in the instruction descriptor
+// for that K block.  So the planes need only be written for the upper super
+// tiles (SqArgs::tri_planes).
 #include <cuda.h>
 #include <cuda_fp16.h>
 
@@ -48,51 +59,42 @@ namespace tc2 {
 
 using namespace sp2::tc;
 
-constexpr int STAGE_SPLIT = 2 * A_BYTES + 2 * B_BYTES;  // 96 KB: hpA loA hpB loB
-constexpr int STAGE_PLAIN = A_BYTES + B_BYTES;          // 48 KB: hiA hiB
-constexpr int STAGES_SPLIT = 2;
-constexpr int STAGES_PLAIN = 4;
+constexpr int BH = BM;                     // 128 rows per CTA of each operand
+constexpr int HALF_BYTES = BH * BK * 2;    // 16 KB: one plane of one operand half
+constexpr int STAGE_SPLIT = 4 * HALF_BYTES;  // 64 KB: hpA loA hpB loB
+constexpr int STAGE_PLAIN = 2 * HALF_BYTES;  // 32 KB: hiA hiB
+constexpr int STAGES_SPLIT = 3;
+constexpr int STAGES_PLAIN = 6;
 constexpr int EPI_WARPS = epi::WARPS;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;  // two 256-column accumulators
 
+// Instruction descriptor of the pair MMA: M = 256 (bits 24-28 = M >> 4),
+// N = 256 (bits 17-22 = N >> 3), D = F32, A = B = F16, K-major unless the
+// MN bits are added.
+constexpr uint32_t IDESC2 = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24);
+
 // one 64 x 64 FP16 box of a transposed read
 constexpr int T_BOX = 64 * 64 * 2;
-// stage offsets (split): hpA, loA (A_BYTES each), hpB, loB (B_BYTES each)
-constexpr int OFF_HPA = 0, OFF_LOA = A_BYTES, OFF_HPB = 2 * A_BYTES, OFF_LOB = 2 * A_BYTES + B_BYTES;
+// stage offsets (split): hpA, loA, hpB, loB
+constexpr int OFF_HPA = 0, OFF_LOA = HALF_BYTES, OFF_HPB = 2 * HALF_BYTES, OFF_LOB = 3 * HALF_BYTES;
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive;\n\tbarrier.cluster.wait;" ::: "memory");
-}
-
-// TMA load multicast to the CTAs in mask: same shared offset in each, each
-// destination CTA's mbarrier at that offset receives the byte count.
-__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, uint64_t* bar,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
-      "[%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-
-// Arrive on the mbarrier at this offset in every CTA of mask once all prior
-// tcgen05 operations of this thread have completed.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                   smem_u32(bar)),
-               "h"(mask)
-               : "memory");
+// Loads one 128-row operand half of K block k0 into dst: K-major (one box of
+// 64 x 128) when the block lies on or right of the diagonal, else the stored
+// block transposed (two boxes of 64 x 64).
+__device__ __forceinline__ void load_half(uint8_t* dst, const CUtensorMap* tmK, const CUtensorMap* tmT, bool trans,
+                                          int row, int k0, int b, uint32_t bar_cl) {
+  if (!trans) {
+    tma_load_3d_pair(dst, tmK, k0, row, b, bar_cl);
+  } else {
+    tma_load_3d_pair(dst, tmT, row, k0, b, bar_cl);
+    tma_load_3d_pair(dst + T_BOX, tmT, row + 64, k0, b, bar_cl);
+  }
 }
 
 // RO: readout mode of the epilogue (finite-temperature expansion).
-// tm_p0T / tm_p1T: the planes with 64 x 64 boxes (transposed reads).
+// tm_p0A/p1A: planes with 64 x 128 boxes (the A half); tm_p0B/p1B: the same
+// boxes for the B half; tm_p0T / tm_p1T: 64 x 64 boxes (transposed reads).
 template <bool SPLIT, bool RO>
 __global__ void __launch_bounds__(THREADS, 1)
     syrk_tc2_kernel(const __grid_constant__ CUtensorMap tm_p0A, const __grid_constant__ CUtensorMap tm_p1A,
@@ -115,40 +117,43 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const uint32_t peer = rank ^ 1u;
 
   if (threadIdx.x == 0) {
     s_abort = 0;
     epi::init(s_epi);
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 2);  // released by both CTAs' MMAs
+      mbar_init(&full[s], 1);   // the even CTA's producer arrive (+ bytes of both CTAs)
+      mbar_init(&empty[s], 1);  // one commit of the MMA issuer
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tmem_full[i], 1);
-      mbar_init(&tmem_empty[i], EPI_WARPS);
+      mbar_init(&tmem_empty[i], 2 * EPI_WARPS);  // epilogue warps of both CTAs
     }
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, TMEM_COLS);
-    tmem_relinquish();
+    tmem_alloc_pair(tmem_slot, TMEM_COLS);
+    tmem_relinquish_pair();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  // the peer's barriers must exist before any multicast reaches them
+  // the peer's barriers must exist before any load, commit or arrive reaches them
   cluster_sync();
   const uint32_t tmem_base = *tmem_slot;
   volatile int* abort_flag = &s_abort;
-  const int rank = (int)cluster_rank();
+  const uint32_t peer_abort = mapa_u32(smem_u32(&s_abort), peer);
   const int cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
   const int nsuper = a.ntiles >> 1;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
+      const uint32_t full_cl = mapa_u32(smem_u32(&full[0]), 0);  // the even CTA's barriers
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -156,52 +161,34 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int s = 0; s < STAGES; ++s) armed[s] = 0;
       for (int u = cl; u < nsuper && ok; u += ncl) {
-        const int t = 2 * u + rank;
         int b, I, J, h;
-        unpack_tile(a.tiles[t], b, I, J, h);
+        unpack_tile(a.tiles[2 * u + (int)rank], b, I, J, h);
         if (!load_params(a, b).active) continue;
         const int N = a.Ns[b];
-        const int rowA = I * BN + h * BM, rowB = J * BN + rank * BM;
+        const int rowA = I * BN + (int)rank * BH, rowB = J * BN + (int)rank * BH;
         const int nk = (N + BK - 1) / BK;
         for (int kb = 0; kb < nk; ++kb) {
-          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+          if (!mbar_wait_cl(&empty[stage], phase ^ 1u, abort_flag)) {
             ok = false;
             break;
           }
           uint8_t* st = smem + stage * STAGE_BYTES;
-          mbar_expect_tx(&full[stage], STAGE_BYTES);
+          if (rank == 0) {
+            mbar_expect_tx(&full[stage], 2 * STAGE_BYTES);
+            ++armed[stage];
+          }
+          const uint32_t bar = full_cl + 8u * (uint32_t)stage;
           const int k0 = kb * BK;
           const int ks = k0 / BN;  // super column of this K block
-          // A rows: K-major from (I, k) on or right of the diagonal, else
-          // the stored (k, I) transposed as two 64 x 64 boxes
-          uint8_t* a0 = st + (SPLIT ? OFF_HPA : 0);
-          if (ks >= I) {
-            tma_load_3d(a0, &tm_p0A, k0, rowA, b, &full[stage]);
-            if (SPLIT) tma_load_3d(st + OFF_LOA, &tm_p1A, k0, rowA, b, &full[stage]);
+          if (SPLIT) {
+            load_half(st + OFF_HPA, &tm_p0A, &tm_p0T, ks < I, rowA, k0, b, bar);
+            load_half(st + OFF_LOA, &tm_p1A, &tm_p1T, ks < I, rowA, k0, b, bar);
+            load_half(st + OFF_HPB, &tm_p0B, &tm_p0T, ks < J, rowB, k0, b, bar);
+            load_half(st + OFF_LOB, &tm_p1B, &tm_p1T, ks < J, rowB, k0, b, bar);
           } else {
-            tma_load_3d(a0, &tm_p0T, rowA, k0, b, &full[stage]);
-            tma_load_3d(a0 + T_BOX, &tm_p0T, rowA + 64, k0, b, &full[stage]);
-            if (SPLIT) {
-              tma_load_3d(st + OFF_LOA, &tm_p1T, rowA, k0, b, &full[stage]);
-              tma_load_3d(st + OFF_LOA + T_BOX, &tm_p1T, rowA + 64, k0, b, &full[stage]);
-            }
+            load_half(st, &tm_p0A, &tm_p0T, ks < I, rowA, k0, b, bar);
+            load_half(st + HALF_BYTES, &tm_p0B, &tm_p0T, ks < J, rowB, k0, b, bar);
           }
-          // this CTA's half of the B rows, multicast into both CTAs
-          uint8_t* b0 = st + (SPLIT ? OFF_HPB : A_BYTES) + rank * (B_BYTES / 2);
-          if (ks >= J) {
-            tma_load_3d_mc(b0, &tm_p0B, k0, rowB, b, &full[stage], 0x3);
-            if (SPLIT)
-              tma_load_3d_mc(st + OFF_LOB + rank * (B_BYTES / 2), &tm_p1B, k0, rowB, b, &full[stage], 0x3);
-          } else {
-            tma_load_3d_mc(b0, &tm_p0T, rowB, k0, b, &full[stage], 0x3);
-            tma_load_3d_mc(b0 + T_BOX, &tm_p0T, rowB + 64, k0, b, &full[stage], 0x3);
-            if (SPLIT) {
-              uint8_t* b1 = st + OFF_LOB + rank * (B_BYTES / 2);
-              tma_load_3d_mc(b1, &tm_p1T, rowB, k0, b, &full[stage], 0x3);
-              tma_load_3d_mc(b1 + T_BOX, &tm_p1T, rowB + 64, k0, b, &full[stage], 0x3);
-            }
-          }
-          ++armed[stage];
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -210,38 +197,51 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       if (!ok || *abort_flag) {
         atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
-        for (int s = 0; s < STAGES; ++s) {
-          if (armed[s] == 0) continue;
+        st_cluster_u32(peer_abort, 1u);
+        if (rank == 0) {
+          // the armed phases complete once both CTAs' bytes have landed
+          for (int s = 0; s < STAGES; ++s) {
+            if (armed[s] == 0) continue;
+            const uint64_t t0 = globaltimer();
+            while (!mbar_try_wait_cl(&full[s], (armed[s] - 1u) & 1u) && globaltimer() - t0 < kTimeoutNs) {
+            }
+          }
+        } else {
+          // the odd CTA's loads complete on the even CTA's barriers, which it
+          // cannot poll: give its last loads time to land before it leaves
           const uint64_t t0 = globaltimer();
-          while (!mbar_try_wait(&full[s], (armed[s] - 1u) & 1u) && globaltimer() - t0 < kTimeoutNs) {
+          while (globaltimer() - t0 < 2000000ull) {
           }
         }
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    if (lane == 0 && rank == 0) {
+      const uint32_t empty_own = smem_u32(&empty[0]);
+      const uint32_t empty_peer = mapa_u32(empty_own, 1);
+      const uint32_t tfull_own = smem_u32(&tmem_full[0]);
+      const uint32_t tfull_peer = mapa_u32(tfull_own, 1);
       int stage = 0;
       uint32_t phase = 0, it = 0;
       bool ok = true, issued = false;
       for (int u = cl; u < nsuper && ok; u += ncl) {
-        const int t = 2 * u + rank;
         int b, I, J, h;
-        unpack_tile(a.tiles[t], b, I, J, h);
+        unpack_tile(a.tiles[2 * u], b, I, J, h);
         if (!load_params(a, b).active) continue;
         const int N = a.Ns[b];
         const int nk = (N + BK - 1) / BK;
         const uint32_t buf = it & 1u;
         (void)h;
-        // the k-th use of a buffer waits for the epilogue's (k-1)-th release
-        if (!mbar_wait(&tmem_empty[buf], ((it >> 1) & 1u) ^ 1u, abort_flag)) {
+        // the k-th use of a buffer waits for the epilogues' (k-1)-th release
+        if (!mbar_wait_cl(&tmem_empty[buf], ((it >> 1) & 1u) ^ 1u, abort_flag)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t d = tmem_base + buf * BN;
         for (int kb = 0; kb < nk; ++kb) {
-          if (!mbar_wait(&full[stage], phase, abort_flag)) {
+          if (!mbar_wait_cl(&full[stage], phase, abort_flag)) {
             ok = false;
             break;
           }
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           // operands left of the diagonal arrived transposed (MN-major)
           const int sc = kb * BK / BN;
           const bool ta = sc < I, tb = sc < J;
-          const uint32_t idesc = IDESC | (ta ? IDESC_A_MN : 0u) | (tb ? IDESC_B_MN : 0u);
+          const uint32_t idesc = IDESC2 | (ta ? IDESC_A_MN : 0u) | (tb ? IDESC_B_MN : 0u);
 #pragma unroll
           for (int ks = 0; ks < BK / UMMA_K; ++ks) {
             // K step ks: 32 B along a K-major row, or two 8-row K groups
@@ -262,16 +262,18 @@ __global__ void __launch_bounds__(THREADS, 1)
               const uint64_t dloA = ta ? make_desc_mn128(st + OFF_LOA + oa) : make_desc_sw128(st + OFF_LOA + oa);
               const uint64_t dhpB = tb ? make_desc_mn128(st + OFF_HPB + ob) : make_desc_sw128(st + OFF_HPB + ob);
               const uint64_t dloB = tb ? make_desc_mn128(st + OFF_LOB + ob) : make_desc_sw128(st + OFF_LOB + ob);
-              mma_f16_id(d, dhpA, dhpB, idesc, acc);  // hp hp
-              mma_f16_id(d, dloA, dhpB, idesc, 1u);   // lo' hp
-              mma_f16_id(d, dhpA, dloB, idesc, 1u);   // hp lo'
+              mma_f16_pair(d, dhpA, dhpB, idesc, acc);  // hp hp
+              mma_f16_pair(d, dloA, dhpB, idesc, 1u);   // lo' hp
+              mma_f16_pair(d, dhpA, dloB, idesc, 1u);   // hp lo'
             } else {
               const uint64_t dA = ta ? make_desc_mn128(st + oa) : make_desc_sw128(st + oa);
-              const uint64_t dB = tb ? make_desc_mn128(st + A_BYTES + ob) : make_desc_sw128(st + A_BYTES + ob);
-              mma_f16_id(d, dA, dB, idesc, acc);
+              const uint64_t dB = tb ? make_desc_mn128(st + HALF_BYTES + ob) : make_desc_sw128(st + HALF_BYTES + ob);
+              mma_f16_pair(d, dA, dB, idesc, acc);
             }
           }
-          mma_commit_mc(&empty[stage], 0x3);  // release the stage in both CTAs
+          // release the stage in both CTAs
+          mma_commit_pair(empty_own + 8u * (uint32_t)stage);
+          mma_commit_pair(empty_peer + 8u * (uint32_t)stage);
           issued = true;
           if (++stage == STAGES) {
             stage = 0;
@@ -279,12 +281,16 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
         if (!ok) break;
-        mma_commit(&tmem_full[buf]);
+        mma_commit_pair(tfull_own + 8u * buf);
+        mma_commit_pair(tfull_peer + 8u * buf);
         ++it;
       }
-      if (!ok) atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
+      if (!ok || *abort_flag) {
+        atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
+        st_cluster_u32(peer_abort, 1u);
+      }
       if (issued) {
-        mma_commit(drain);
+        mma_commit_pair(smem_u32(drain));
         const uint64_t t0 = globaltimer();
         while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
         }
@@ -294,12 +300,16 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ------------------------------------------------------------ epilogue
     const int ew = warp - 2;  // 0..7
     const int q = warp & 3;   // TMEM lane quarter
+    const uint32_t empty_cl = mapa_u32(smem_u32(&tmem_empty[0]), 0);
     uint32_t it = 0;
     for (int u = cl; u < nsuper; u += ncl) {
-      const int t = 2 * u + rank;
-      const int rc = epi::tile<SPLIT, false, RO>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag, s_epi, ew, q,
-                                                  lane);
-      if (rc < 0) break;
+      const int t = 2 * u + (int)rank;
+      const int rc = epi::tile<SPLIT, false, RO, true>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag, s_epi,
+                                                        ew, q, lane, empty_cl);
+      if (rc < 0) {
+        if (lane == 0) st_cluster_u32(peer_abort, 1u);
+        break;
+      }
       it += (uint32_t)rc;
     }
   }
@@ -307,11 +317,12 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  // no CTA leaves while its peer may still multicast into it or arrive on it
+  // neither CTA leaves (or frees its tensor memory) while the pair's MMAs,
+  // loads or arrivals may still reach it
   cluster_sync();
   if (warp == 1) {
     __syncwarp();
-    tmem_dealloc(tmem_base, TMEM_COLS);
+    tmem_dealloc_pair(tmem_base, TMEM_COLS);
   }
 }
 
