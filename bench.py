@@ -59,6 +59,9 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--gen-device", default="gpu", choices=["gpu", "cpu"],
                     help="where the input generator runs its FP64 QR (cpu: for runs under a profiler)")
+    ap.add_argument("--input-cache", default=None,
+                    help="directory: reuse the generated Hamiltonian (H, Q, eps) stored there by an earlier run, "
+                         "else generate and store it (profiled runs then need no QR)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-SP2 measurement")
     ap.add_argument("--no-network", action="store_true", help="skip the network forward/backward measurement")
@@ -74,6 +77,25 @@ def _workload(n):
     if n != w["N"]:
         w["N"], w["n_occ"] = n, n // 2
     return w
+
+
+def _cached_input(cache_dir, w, make):
+    """The workload's Hamiltonian, from cache_dir when an earlier run stored
+    it there (same N, occupation, spectrum intervals and seed), else made
+    and, with a cache_dir, stored."""
+    if not cache_dir:
+        return make()
+    import sp2_inputs
+
+    key = f"sp2_input_N{w['N']}_occ{w['n_occ']}_{w['occ'][0]}_{w['occ'][1]}_{w['virt'][0]}_{w['virt'][1]}_s{w['seed']}"
+    path = os.path.join(cache_dir, key + ".npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return sp2_inputs.Hamiltonian(H=z["H"], Q=z["Q"], eps=z["eps"], n_occ=int(z["n_occ"]), seed=int(z["seed"]))
+    h = make()
+    os.makedirs(cache_dir, exist_ok=True)
+    np.savez(path, H=h.H, Q=h.Q, eps=h.eps, n_occ=h.n_occ, seed=h.seed)
+    return h
 
 
 def _peaks():
@@ -313,20 +335,36 @@ def _bench_batched(sp2, sp2_inputs, dev, reps=3, count=512):
     layers = [s.iterations + 2 for s in st]
     flops = sum(l * 2.0 * c[0] ** 3 for l, c in zip(layers, cfg))
     alg = sum(l * 3.0 * c[0] ** 3 for l, c in zip(layers, cfg))
+    # per-instance accuracy on a seeded sample of instances: the whole D
+    # against Q_occ Q_occ^T of the generator (Eq. 6), outside the timed region
+    Ds, _ = sp2.density_matrix_batched(Hs, n_occ)
+    torch.cuda.synchronize(dev)
+    pick = np.random.default_rng(5).choice(len(cfg), size=min(16, len(cfg)), replace=False)
+    errs, tr_errs = [], []
+    for i in sorted(pick):
+        N, n, g, sd = cfg[i]
+        h = sp2_inputs.batched_instance(N, n, g, sd)
+        Qo = h.Q[:, :n]
+        Di = Ds[i].cpu().numpy().astype(np.float64)
+        errs.append(float(np.max(np.abs(Di - Qo @ Qo.T))))
+        tr_errs.append(abs(float(np.trace(Di)) - n))
     return {"instances": len(cfg), "ms": ms, "tflops_2n3": flops / (ms * 1e-3) / 1e12,
             "tflops_split_alg_3n3": alg / (ms * 1e-3) / 1e12, "layers_min": min(layers),
             "layers_mean": float(np.mean(layers)), "layers_max": max(layers),
-            "all_converged": all(s.status == 0 for s in st)}
+            "all_converged": all(s.status == 0 for s in st),
+            "accuracy": {"instances_checked": len(errs), "sizes": [int(cfg[i][0]) for i in sorted(pick)],
+                         "max_abs_err_worst": max(errs), "max_abs_err_median": float(np.median(errs)),
+                         "trace_err_worst": max(tr_errs), "reference": "closed form Q_occ Q_occ^T, whole D"}}
 
 
-def _bench_network(sp2, sp2_inputs, dev, B=64, N=2048, L=20, ckpt_every=5, reps=2):
+def _bench_network(sp2, sp2_inputs, dev, B=64, N=2048, L=20, ckpt_every=5, reps=2, grad_check=True):
     """Differentiable network: 64 gapped Hamiltonians of N = 2048, 20 layers,
     coefficients initialised to the SP2 branch values of instance 0."""
     import torch
 
-    Hs = [sp2_inputs.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), 2000 + i, device=str(dev)).h32()
+    hs = [sp2_inputs.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), 2000 + i, device=str(dev))
           for i in range(B)]
-    H = torch.from_numpy(np.stack(Hs)).to(dev)
+    H = torch.from_numpy(np.stack([x.h32() for x in hs])).to(dev)
     _, st = sp2.density_matrix(H[0].contiguous(), N // 2, precision="split")
     sig = st.sigmas + [1 if k % 2 == 0 else -1 for k in range(L)]
     coef = torch.tensor([[1.0, 0.0, 0.0] if s > 0 else [-1.0, 2.0, 0.0] for s in sig[:L]], dtype=torch.float32)
@@ -349,8 +387,70 @@ def _bench_network(sp2, sp2_inputs, dev, B=64, N=2048, L=20, ckpt_every=5, reps=
     f_fwd = B * L * 3.0 * N ** 3
     # backward: recomputation of the non-checkpointed layers + the split SYR2K (6 N^3 per layer)
     f_bwd = B * (L - (L + ckpt_every - 1) // ckpt_every) * 3.0 * N ** 3 + B * L * 6.0 * N ** 3
-    return {"B": B, "N": N, "layers": L, "ckpt_every": ckpt_every, "forward_ms": fwd, "backward_ms": bwd,
-            "forward_tflops_alg": f_fwd / (fwd * 1e-3) / 1e12, "backward_tflops_alg": f_bwd / (bwd * 1e-3) / 1e12}
+    out = {"B": B, "N": N, "layers": L, "ckpt_every": ckpt_every, "forward_ms": fwd, "backward_ms": bwd,
+           "forward_tflops_alg": f_fwd / (fwd * 1e-3) / 1e12, "backward_tflops_alg": f_bwd / (bwd * 1e-3) / 1e12}
+    if grad_check:
+        out["gradient_check"] = _network_grad_check(sp2, sp2_inputs, dev, H, hs, coef, ckpt_every)
+    return out
+
+
+def _network_grad_check(sp2, sp2_inputs, dev, H, hs, coef, ckpt_every, sub=2, h=1e-4):
+    """Gradient errors of the network (outside any timed region), with the
+    loss of reading C16 against the Fermi-Dirac target (kT = 0.05, mu = 0):
+    (a) the adjoint's dL/dcoef on the whole batch against central differences
+    of the GPU forward (loss summed in FP64) on six coefficients; (b) the
+    adjoint on a sub-batch against the FP64 oracle's adjoint (the oracle is
+    test infrastructure: a CPU reference, not part of the timed path)."""
+    import torch
+
+    import oracle
+
+    B, N = H.shape[0], H.shape[1]
+    L = coef.shape[0]
+    T = torch.empty((B, N, N), dtype=torch.float64, device=dev)
+    for b, x in enumerate(hs):
+        Q = torch.from_numpy(x.Q).to(dev)
+        occ = 1.0 / (1.0 + torch.exp(torch.from_numpy(x.eps).to(dev) / 0.05))
+        T[b] = (Q * occ[None, :]) @ Q.T
+    del Q
+    X, ck, _ = sp2.network_forward(H, coef, ckpt_every)
+    G_L = (2.0 * (X.double() - T) / B).float().contiguous()
+    dcoef, _ = sp2.network_backward(H, coef, ckpt_every, ck, G_L)
+    d = dcoef.numpy().astype(np.float64)
+
+    def loss(cf):
+        Xc, _, _ = sp2.network_forward(H, cf, ckpt_every)
+        return float(((Xc.double() - T) ** 2).sum().item() / B)
+
+    c32 = coef.numpy().astype(np.float32)
+    fd_errs = []
+    for n, k in [(0, 0), (0, 1), (L // 4, 2), (L // 2, 0), (3 * L // 4, 1), (L - 1, 2)]:
+        cp, cm = c32.copy(), c32.copy()
+        cp[n, k] = np.float32(c32[n, k] + h)
+        cm[n, k] = np.float32(c32[n, k] - h)
+        fd = (loss(torch.from_numpy(cp)) - loss(torch.from_numpy(cm))) / (float(cp[n, k]) - float(cm[n, k]))
+        fd_errs.append(abs(fd - d[n, k]) / np.max(np.abs(d)))
+    del X, ck, G_L
+    # (b) sub-batch against the FP64 oracle adjoint
+    Hs = H[:sub].contiguous()
+    Xs, cks, _ = sp2.network_forward(Hs, coef, ckpt_every)
+    X0 = []
+    for x in hs[:sub]:
+        H64 = x.h32().astype(np.float64)
+        lo, hi = oracle.gershgorin_bounds(H64)
+        X0.append(oracle.input_layer(H64, lo, hi))
+    X0 = np.stack(X0)
+    Ts = T[:sub].cpu().numpy()
+    GLs = (2.0 * (Xs.cpu().numpy().astype(np.float64) - Ts) / sub).astype(np.float32)
+    ds, G0 = sp2.network_backward(Hs, coef, ckpt_every, cks, torch.from_numpy(GLs).to(dev))
+    want_d, want_G0 = oracle.network_adjoint(X0, coef.numpy().astype(np.float64), GLs.astype(np.float64))
+    return {"fd_step": h, "fd_coefficients": 6,
+            "dcoef_err_vs_central_differences_rel_to_max": float(max(fd_errs)),
+            "oracle_sub_batch": sub,
+            "dcoef_err_vs_fp64_adjoint_rel_to_max": float(np.max(np.abs(ds.numpy() - want_d)) / np.max(np.abs(want_d))),
+            "dX0_err_vs_fp64_adjoint_rel_to_max": float(np.max(np.abs(G0.cpu().numpy() - want_G0))
+                                                     / np.max(np.abs(want_G0))),
+            "loss": "(1/B) sum ||X_L - D_FD||_F^2, D_FD at kT = 0.05, mu = 0"}
 
 
 def _bench_fermi(sp2, sp2_inputs, dev, B=64, N=2048, L=11, reps=3):
@@ -396,7 +496,8 @@ def run_ours(args):
     N, n_occ = w["N"], w["n_occ"]
     t_gen = time.perf_counter()
     gen_dev = str(dev) if args.gen_device == "gpu" else "cpu"
-    h = sp2_inputs.gapped_hamiltonian(N, n_occ, w["occ"], w["virt"], w["seed"], device=gen_dev)
+    h = _cached_input(args.input_cache, w, lambda: sp2_inputs.gapped_hamiltonian(
+        N, n_occ, w["occ"], w["virt"], w["seed"], device=gen_dev))
     t_gen = time.perf_counter() - t_gen
     H32 = h.h32()
     H = torch.from_numpy(H32).to(dev)

@@ -131,6 +131,29 @@ sp2_status sp2_set_precision(int precision);
 const char* sp2_last_error(void);
 
 /*
+ * Fault injection for tests of the error paths (failure detection; the
+ * paper has no counterpart).  spec is a comma-separated list; NULL, "" or
+ * "none" clears every fault.  Items:
+ *   alloc_fail  the library's next workspace request fails as if cudaMalloc
+ *               had run out of memory: the call returns SP2_ERR_OOM before it
+ *               enqueues any work (D_out untouched)
+ *   nan_input   the next sp2_density_matrix / _accelerated reads row 0 of H
+ *               as holding a NaN: SP2_ERR_NONFINITE, no layer runs
+ *   timeout     in the next single-matrix solve's first squaring launch the
+ *               MMA issuer waits on a barrier that nothing arrives on; the
+ *               wait runs out, every CTA stops issuing, drains its copies and
+ *               MMAs, frees its tensor memory and returns; the call returns
+ *               SP2_ERR_DEVICE_TIMEOUT (D_out holds no meaningful values)
+ *   wait_ms=<n> bound of every device wait of the tensor-core squaring
+ *               kernels, 1..60000 ms (default 4000); stays in force
+ * alloc_fail, nan_input and timeout each fire once.  The environment variable
+ * SP2_FAULT, when set, is applied by sp2_init.  Needs neither a GPU nor
+ * sp2_init.  Returns SP2_ERR_INVALID_ARG (and changes nothing) for an unknown
+ * or malformed item.  Nothing here faults, traps or hangs a GPU.
+ */
+sp2_status sp2_set_fault(const char* spec);
+
+/*
  * Zero-temperature density matrix D = theta(mu I - H) with Tr D = N_occ by
  * Deep-NN SP2 (Alg. 1) with the refinement layer f_final (Eq. 15).
  *
@@ -299,8 +322,13 @@ sp2_status sp2_observable(const float* D, const float* A, int N, double* out);
  *            ("N exceeds SP2_NOALLOC_MAX_N" in sp2_last_error()).
  *   stream   cudaStream_t to enqueue on (NULL = legacy default stream).
  * Split-FP16 precision with the sp2_init defaults (shift on, epsilon 0,
- * low-part scale 2^11); needs no sp2_init.  stats->time_ms and layer_ms are
- * not measured (0).  The first call on a device, with that device current,
+ * low-part scale 2^11); needs no sp2_init.  stats->time_ms, layer_ms,
+ * square_ms, prologue_ms and energy are not measured (0).  With stats ==
+ * NULL the call returns once the work is enqueued and its status reflects
+ * the argument checks only: a device-side failure (non-finite H, degenerate
+ * spectrum, a timed-out wait) is reported only through a call with stats,
+ * whose read-back synchronises the stream (refused with SP2_ERR_INVALID_ARG
+ * on a stream that is being captured).  The first call on a device, with that device current,
  * looks up the array's device address (cudaGetSymbolAddress); make that first
  * call before any stream capture.  All calls share the array and leave their
  * contents in it (the zero-start counters are cleared at the start of each

@@ -162,6 +162,7 @@ def _load():
         "sp2_split": (_I, [_P, _I, _I, _P, _P]),
         "sp2_layer": (_I, [_P, _I, _I, _F, _F, _F, _P, _P]),
         "sp2_observable": (_I, [_P, _P, _I, _P]),
+        "sp2_set_fault": (_I, [ctypes.c_char_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -186,6 +187,13 @@ def init(device: int = 0, precision: str = "split", lo_scale_exp: int = 11, shif
     _check(lib.sp2_init(ctypes.byref(cfg)))
     _state["device"] = device
     _state["precision"] = precision
+
+
+def set_fault(spec: Optional[str]) -> None:
+    """Arms injected faults for tests of the error paths: "alloc_fail",
+    "nan_input", "timeout", "wait_ms=<n>" (comma-separated; None or "none"
+    clears).  See sp2_set_fault in include/sp2.h."""
+    _check(_load().sp2_set_fault(None if spec is None else spec.encode()))
 
 
 def finalize() -> None:

@@ -103,11 +103,22 @@ struct State {
   int batched_sched = 0;
   std::map<uint64_t, int> batched_choice;
   std::vector<uint64_t> bgraph_key;
+  // injected faults (sp2_set_fault / SP2_FAULT): each fires once
+  bool fault_alloc = false, fault_nan = false, fault_stall = false;
+  // side of the square groups of the tile order (SP2_TILE_GROUP, default 8)
+  int tile_group = 8;
+  unsigned long long wait_ns = 0;  // bound of the squaring kernels' waits (0: 4 s)
 };
 
 State g;
 
 sp2_status ws(BufId id, size_t bytes, void** out, bool zero = false) {
+  if (g.fault_alloc) {
+    g.fault_alloc = false;
+    set_err("injected allocation failure (fault alloc_fail): the workspace request of %zu bytes was refused",
+            bytes);
+    return SP2_ERR_OOM;
+  }
   Buf& b = g.buf[id];
   if (bytes == 0) bytes = 16;
   if (b.bytes < bytes) {
@@ -158,7 +169,7 @@ inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m
 // (adjacent; the CTA-pair kernel takes them together).
 void build_tiles(int N, int B, int tile, int halves, std::vector<uint32_t>& out, int& per_instance) {
   const int T = (N + tile - 1) / tile;
-  const int G = 8;
+  const int G = g.tile_group;
   std::vector<uint32_t> one;
   for (int gi = 0; gi < T; gi += G)
     for (int gj = gi; gj < T; gj += G)
@@ -347,8 +358,47 @@ sp2_status status_of(const Ctl& c, int dev_err) {
 
 extern "C" {
 
+sp2_status sp2_set_fault(const char* spec) {
+  t_err.clear();
+  bool alloc = false, nan = false, stall = false;
+  unsigned long long wait_ns = 0;
+  const std::string sp = spec ? spec : "";
+  size_t pos = 0;
+  while (pos <= sp.size()) {
+    size_t end = sp.find(',', pos);
+    if (end == std::string::npos) end = sp.size();
+    const std::string item = sp.substr(pos, end - pos);
+    if (item.empty() || item == "none") {
+    } else if (item == "alloc_fail") {
+      alloc = true;
+    } else if (item == "nan_input") {
+      nan = true;
+    } else if (item == "timeout") {
+      stall = true;
+    } else if (item.compare(0, 8, "wait_ms=") == 0) {
+      char* e = nullptr;
+      const long v = std::strtol(item.c_str() + 8, &e, 10);
+      if (!e || *e != '\0' || e == item.c_str() + 8 || v < 1 || v > 60000) {
+        set_err("sp2_set_fault: wait_ms must be an integer in [1, 60000], got '%s'", item.c_str() + 8);
+        return SP2_ERR_INVALID_ARG;
+      }
+      wait_ns = (unsigned long long)v * 1000000ull;
+    } else {
+      set_err("sp2_set_fault: unknown item '%s' (alloc_fail, nan_input, timeout, wait_ms=<n>, none)", item.c_str());
+      return SP2_ERR_INVALID_ARG;
+    }
+    pos = end + 1;
+  }
+  g.fault_alloc = alloc;
+  g.fault_nan = nan;
+  g.fault_stall = stall;
+  g.wait_ns = wait_ns;
+  return SP2_OK;
+}
+
 sp2_status sp2_init(const sp2_config* cfg) {
   t_err.clear();
+  if (const char* fs = getenv("SP2_FAULT")) CKS(sp2_set_fault(fs));
   sp2_config c;
   c.device = 0;
   c.stream = nullptr;
@@ -402,6 +452,10 @@ sp2_status sp2_init(const sp2_config* cfg) {
     g.batched_sched = (bk && strcmp(bk, "single") == 0) ? 1 : (bk && strcmp(bk, "pairs") == 0) ? 2 : 0;
     const char* gv = getenv("SP2_GRAPHS");
     g.use_graphs = !(gv && strcmp(gv, "0") == 0);
+    const char* tg = getenv("SP2_TILE_GROUP");
+    const int tgv = tg ? atoi(tg) : 8;
+    if (tgv != g.tile_group) g.tiles_key_N = -1;
+    g.tile_group = (tgv >= 1 && tgv <= 64) ? tgv : 8;
   }
   g.device = c.device;
   g.stream = (cudaStream_t)c.stream;
@@ -554,6 +608,7 @@ sp2_status sp2_layer(const float* X, int B, int N, float a, float b, float c, fl
 
   SqArgs A;
   memset(&A, 0, sizeof(A));
+  A.wait_ns = g.wait_ns;
   A.Yin = X;
   A.Yout = X_out;
   A.ld_y = N;
@@ -673,6 +728,7 @@ sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int
 
   SqArgs A;
   memset(&A, 0, sizeof(A));
+  A.wait_ns = g.wait_ns;
   A.Dptr = (float* const*)dptr;
   A.Ns = (const int*)ns;
   A.tiles = (const uint32_t*)g.buf[B_TILES].p;
@@ -696,7 +752,9 @@ sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int
   }
 
   CK(cudaEventRecord(g.ev0, st));
-  CK(launch_gershgorin(H, N, N, (long long)N * N, 1, (double2*)part, (unsigned*)tick, (Ctl*)ctl, nullptr, ggrid, st));
+  CK(launch_gershgorin(H, N, N, (long long)N * N, 1, (double2*)part, (unsigned*)tick, (Ctl*)ctl, nullptr, ggrid, st,
+                       g.fault_nan ? 0 : -1));
+  g.fault_nan = false;
 
   if (tc) {
     const long long ld_h = round_up(N, 64), slot_h = ld_h * N;
@@ -737,6 +795,8 @@ sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int
       A.lo_out = (__half*)lo[cur ^ 1];
       A.hp_out = (__half*)hp[cur ^ 1];
       rnp_step(A, rnp, k);
+      A.stall = (k == 0 && g.fault_stall) ? 1 : 0;
+      g.fault_stall = false;
       if (g.pair_kernel)
         CK(launch_syrk_tc2(A, m[cur], split, grid, st));
       else
@@ -930,6 +990,7 @@ sp2_status batched_once(const float* const* H, const int* N, const int* N_occ, i
 
   SqArgs A;
   memset(&A, 0, sizeof(A));
+  A.wait_ns = g.wait_ns;
   A.Dptr = (float* const*)dptr;
   A.Ns = (const int*)ns;
   A.tiles = (const uint32_t*)dt;
@@ -1354,6 +1415,7 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
   const long long slot = (long long)N * N;
   SqArgs A;
   memset(&A, 0, sizeof(A));
+  A.wait_ns = g.wait_ns;
   A.Dptr = (float* const*)dptr;
   A.Ns = (const int*)ns;
   A.tiles = (const uint32_t*)g.buf[B_TILES].p;
@@ -1536,6 +1598,7 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
   const float ls = std::ldexp(1.0f, g.lo_scale_exp);
   SqArgs A;
   memset(&A, 0, sizeof(A));
+  A.wait_ns = g.wait_ns;
   A.Dptr = (float* const*)dptr;
   A.Ns = (const int*)ns;
   A.tiles = (const uint32_t*)g.buf[B_TILES].p;
@@ -1789,6 +1852,7 @@ sp2_status sp2_fermi_expansion(const float* H, int B, int N, int L, const double
 
   SqArgs A;
   memset(&A, 0, sizeof(A));
+  A.wait_ns = g.wait_ns;
   A.Dptr = (float* const*)dptr;
   A.Ns = (const int*)ns;
   A.tiles = (const uint32_t*)g.buf[B_TILES].p;

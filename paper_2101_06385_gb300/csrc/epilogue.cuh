@@ -150,8 +150,9 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
   }
 
   const uint32_t buf = it & 1u;
-  const bool got = __all_sync(0xffffffffu, PAIR ? mbar_wait_cl(&tmem_full[buf], (it >> 1) & 1u, abort_flag)
-                                                : mbar_wait(&tmem_full[buf], (it >> 1) & 1u, abort_flag));
+  const unsigned long long lim = wait_limit(a);
+  const bool got = __all_sync(0xffffffffu, PAIR ? mbar_wait_cl(&tmem_full[buf], (it >> 1) & 1u, abort_flag, lim)
+                                                : mbar_wait(&tmem_full[buf], (it >> 1) & 1u, abort_flag, lim));
   if (!got) {
     if (lane == 0) atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
     *abort_flag = 1;

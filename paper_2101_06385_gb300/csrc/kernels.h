@@ -71,6 +71,9 @@ struct SqArgs {
   float lo_scale;          // 2^s
   float lo_unscale;        // 2^-s
   int* err;                // device error word (SP2_ERR_DEVICE_TIMEOUT on a timed-out wait)
+  unsigned long long wait_ns;  // bound of every mbarrier wait of the tcgen05 kernels (0: 4 s)
+  int stall;               // fault injection: the MMA issuer first waits on a barrier that
+                           // nothing arrives on, so that wait runs out after wait_ns
 };
 
 // tensor-core tile geometry
@@ -78,8 +81,11 @@ constexpr int kTcBM = 128;   // rows per CTA tile (TMEM lanes)
 constexpr int kTcBN = 256;   // columns per CTA tile; 256 x 256 "super tiles" hold two CTA tiles
 constexpr int kSimtB = 128;  // FFMA tile
 
+// nan_row >= 0 (fault injection): that row of the stacked instances is
+// treated as holding a NaN.
 cudaError_t launch_gershgorin(const float* H, int N, long long ld, long long slot, int B, double2* partials,
-                              unsigned* ticket, Ctl* ctl, double* bounds_out, int grid, cudaStream_t st);
+                              unsigned* ticket, Ctl* ctl, double* bounds_out, int grid, cudaStream_t st,
+                              long long nan_row = -1);
 cudaError_t launch_gershgorin_batched(const float* const* Hs, const int* Ns, Ctl* ctl, int batch, double2* partials,
                                      unsigned* tickets, int grid_x, cudaStream_t st);
 cudaError_t launch_input_layer(const float* const* Hs, const int* Ns, long long ld_in, float* Y, long long ld_y,

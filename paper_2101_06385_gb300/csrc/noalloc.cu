@@ -26,8 +26,10 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/sp2.h"
 #include "common.cuh"
@@ -125,12 +127,14 @@ __global__ void init_kernel(unsigned char* base, const float* H, float* D, int N
 }
 
 struct DeviceState {
-  bool ready = false;
+  std::atomic<bool> ready{false};
   unsigned char* scratch = nullptr;
   int num_sms = 0;
 };
 DeviceState g_dev[64];
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+// serialises the one-time set-up (host threads making their first calls at once)
+std::mutex g_setup;
 
 // the text sp2_last_error() returns
 void msg(const char* s) { set_error_text(s); }
@@ -179,34 +183,47 @@ extern "C" sp2_status sp2_density_matrix_noalloc(const float* H, int N, int N_oc
     return SP2_ERR_UNSUPPORTED;
   }
   DeviceState& ds = g_dev[dev];
-  if (!ds.ready) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_sp2_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      msg("sp2_density_matrix_noalloc: cudaGetSymbolAddress of the scratch array failed");
-      return SP2_ERR_CUDA;
-    }
-    int major = 0;
-    NA_CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
-    if (major != 10) {
-      msg("sp2_density_matrix_noalloc: needs an sm_103a device");
-      return SP2_ERR_UNSUPPORTED;
-    }
-    NA_CK(cudaDeviceGetAttribute(&ds.num_sms, cudaDevAttrMultiProcessorCount, dev));
-    if (!g_encode) {
-      void* fn = nullptr;
-      cudaDriverEntryPointQueryResult q;
-      NA_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
-      if (!fn || q != cudaDriverEntryPointSuccess) {
-        msg("sp2_density_matrix_noalloc: cuTensorMapEncodeTiled not available");
+  if (!ds.ready.load(std::memory_order_acquire)) {
+    std::lock_guard<std::mutex> lock(g_setup);
+    if (!ds.ready.load(std::memory_order_relaxed)) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_sp2_noalloc_scratch);
+      if (e != cudaSuccess || p == nullptr) {
+        msg("sp2_density_matrix_noalloc: cudaGetSymbolAddress of the scratch array failed");
+        return SP2_ERR_CUDA;
+      }
+      int major = 0;
+      NA_CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+      if (major != 10) {
+        msg("sp2_density_matrix_noalloc: needs an sm_103a device");
         return SP2_ERR_UNSUPPORTED;
       }
-      g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+      NA_CK(cudaDeviceGetAttribute(&ds.num_sms, cudaDevAttrMultiProcessorCount, dev));
+      if (!g_encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        NA_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (!fn || q != cudaDriverEntryPointSuccess) {
+          msg("sp2_density_matrix_noalloc: cuTensorMapEncodeTiled not available");
+          return SP2_ERR_UNSUPPORTED;
+        }
+        g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+      }
+      ds.scratch = static_cast<unsigned char*>(p);
+      ds.ready.store(true, std::memory_order_release);
     }
-    ds.scratch = static_cast<unsigned char*>(p);
-    ds.ready = true;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  if (stats) {
+    // the stats read-back copies to the host and synchronises the stream,
+    // which a stream under capture does not allow
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    NA_CK(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+      msg("sp2_density_matrix_noalloc: stats must be NULL on a stream that is being captured");
+      return SP2_ERR_INVALID_ARG;
+    }
+  }
   unsigned char* base = ds.scratch;
   __half* hi[2] = {reinterpret_cast<__half*>(base + OFF_HI0), reinterpret_cast<__half*>(base + OFF_HI1)};
   __half* lo[2] = {reinterpret_cast<__half*>(base + OFF_LO0), reinterpret_cast<__half*>(base + OFF_LO1)};

@@ -24,7 +24,7 @@ namespace sp2 {
 __global__ void __launch_bounds__(256) gershgorin_kernel(const float* __restrict__ H, int N, long long ld,
                                                          long long slot, int B, double2* __restrict__ partials,
                                                          unsigned* __restrict__ ticket, Ctl* ctl,
-                                                         double* bounds_out) {
+                                                         double* bounds_out, long long nan_row) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long rows_total = (long long)N * B;
   double lo = INFINITY, hi = -INFINITY;
@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(256) gershgorin_kernel(const float* __restrict
     const double d = (double)row[i];
     const double R = acc - fabs(d);
     if (!isfinite(R) || !isfinite(d)) bad = true;  // fmin/fmax would drop a NaN
+    if (gr == nan_row) bad = true;                    // injected fault: this row reads as holding a NaN
     lo = fmin(lo, d - R);
     hi = fmax(hi, d + R);
   }
@@ -657,8 +658,9 @@ __global__ void __launch_bounds__(256) observable_kernel(const float* __restrict
 
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_gershgorin(const float* H, int N, long long ld, long long slot, int B, double2* partials,
-                              unsigned* ticket, Ctl* ctl, double* bounds_out, int grid, cudaStream_t st) {
-  gershgorin_kernel<<<grid, 256, 0, st>>>(H, N, ld, slot, B, partials, ticket, ctl, bounds_out);
+                              unsigned* ticket, Ctl* ctl, double* bounds_out, int grid, cudaStream_t st,
+                              long long nan_row) {
+  gershgorin_kernel<<<grid, 256, 0, st>>>(H, N, ld, slot, B, partials, ticket, ctl, bounds_out, nan_row);
   return cudaGetLastError();
 }
 

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* tmem_full = empty + STAGES;   // [2]
   uint64_t* tmem_empty = tmem_full + 2;   // [2]
   uint64_t* drain = tmem_empty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* never = drain + 1;  // fault injection: nothing arrives on it
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   __shared__ int s_abort;
   __shared__ epi::Shared s_epi;
 
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&tmem_empty[i], EPI_WARPS);
     }
     mbar_init(drain, 1);
+    mbar_init(never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -95,6 +97,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   volatile int* abort_flag = &s_abort;
+  const unsigned long long lim = wait_limit(a);
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int rowA = I * BN + h * BM, rowB = J * BN;
         const int nk = (N + BK - 1) / BK;
         for (int kb = 0; kb < nk * NSEG; ++kb) {
-          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, lim)) {
             ok = false;
             break;
           }
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int s = 0; s < STAGES; ++s) {
           if (armed[s] == 0) continue;
           const uint64_t t0 = globaltimer();
-          while (!mbar_try_wait(&full[s], (armed[s] - 1u) & 1u) && globaltimer() - t0 < kTimeoutNs) {
+          while (!mbar_try_wait(&full[s], (armed[s] - 1u) & 1u) && globaltimer() - t0 < lim) {
           }
         }
       }
@@ -155,6 +158,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       int stage = 0;
       uint32_t phase = 0, it = 0;
       bool ok = true, issued = false;
+      // injected fault (SqArgs::stall): a wait that runs out after lim
+      if (a.stall && !mbar_wait(never, 0, abort_flag, lim)) ok = false;
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         int b, I, J, h;
         unpack_tile(a.tiles[t], b, I, J, h);
@@ -163,14 +168,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int nk = (N + BK - 1) / BK;
         const uint32_t buf = it & 1u;
         // the k-th use of a buffer waits for the epilogue's (k-1)-th release
-        if (!mbar_wait(&tmem_empty[buf], ((it >> 1) & 1u) ^ 1u, abort_flag)) {
+        if (!mbar_wait(&tmem_empty[buf], ((it >> 1) & 1u) ^ 1u, abort_flag, lim)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t d = tmem_base + buf * BN;
         for (int kb = 0; kb < nk * NSEG; ++kb) {
-          if (!mbar_wait(&full[stage], phase, abort_flag)) {
+          if (!mbar_wait(&full[stage], phase, abort_flag, lim)) {
             ok = false;
             break;
           }
@@ -205,7 +210,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (issued) {
         mma_commit(drain);
         const uint64_t t0 = globaltimer();
-        while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+        while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < lim) {
         }
       }
     }

@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* tmem_full = empty + STAGES;   // [2]
   uint64_t* tmem_empty = tmem_full + 2;   // [2]
   uint64_t* drain = tmem_empty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* never = drain + 1;  // fault injection: nothing arrives on it
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   __shared__ int s_abort;
   __shared__ epi::Shared s_epi;
 
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&tmem_empty[i], 2 * EPI_WARPS);  // epilogue warps of both CTAs
     }
     mbar_init(drain, 1);
+    mbar_init(never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   cluster_sync();
   const uint32_t tmem_base = *tmem_slot;
   volatile int* abort_flag = &s_abort;
+  const unsigned long long lim = wait_limit(a);
   const uint32_t peer_abort = mapa_u32(smem_u32(&s_abort), peer);
   const int cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
   const int nsuper = a.ntiles >> 1;
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int rowA = I * BN + (int)rank * BH, rowB = J * BN + (int)rank * BH;
         const int nk = (N + BK - 1) / BK;
         for (int kb = 0; kb < nk; ++kb) {
-          if (!mbar_wait_cl(&empty[stage], phase ^ 1u, abort_flag)) {
+          if (!mbar_wait_cl(&empty[stage], phase ^ 1u, abort_flag, lim)) {
             ok = false;
             break;
           }
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int s = 0; s < STAGES; ++s) {
             if (armed[s] == 0) continue;
             const uint64_t t0 = globaltimer();
-            while (!mbar_try_wait_cl(&full[s], (armed[s] - 1u) & 1u) && globaltimer() - t0 < kTimeoutNs) {
+            while (!mbar_try_wait_cl(&full[s], (armed[s] - 1u) & 1u) && globaltimer() - t0 < lim) {
             }
           }
         } else {
@@ -225,6 +228,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       int stage = 0;
       uint32_t phase = 0, it = 0;
       bool ok = true, issued = false;
+      // injected fault (SqArgs::stall): a wait that runs out after lim
+      if (a.stall && !mbar_wait(never, 0, abort_flag, lim)) ok = false;
       for (int u = cl; u < nsuper && ok; u += ncl) {
         int b, I, J, h;
         unpack_tile(a.tiles[2 * u], b, I, J, h);
@@ -234,14 +239,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t buf = it & 1u;
         (void)h;
         // the k-th use of a buffer waits for the epilogues' (k-1)-th release
-        if (!mbar_wait_cl(&tmem_empty[buf], ((it >> 1) & 1u) ^ 1u, abort_flag)) {
+        if (!mbar_wait_cl(&tmem_empty[buf], ((it >> 1) & 1u) ^ 1u, abort_flag, lim)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t d = tmem_base + buf * BN;
         for (int kb = 0; kb < nk; ++kb) {
-          if (!mbar_wait_cl(&full[stage], phase, abort_flag)) {
+          if (!mbar_wait_cl(&full[stage], phase, abort_flag, lim)) {
             ok = false;
             break;
           }
@@ -292,7 +297,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (issued) {
         mma_commit_pair(smem_u32(drain));
         const uint64_t t0 = globaltimer();
-        while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+        while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < lim) {
         }
       }
     }

@@ -59,14 +59,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: false on time-out or when another warp of the CTA aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait: false on time-out (limit ns) or when another warp of the CTA aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long limit = kTimeoutNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (globaltimer() - t0 > kTimeoutNs) {
+    if (globaltimer() - t0 > limit) {
       *abort_flag = 1;
       return false;
     }
@@ -220,13 +221,14 @@ __device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* bar, uint32_t parity)
   return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_cl(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                             unsigned long long limit = kTimeoutNs) {
   if (mbar_try_wait_cl(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     if (mbar_try_wait_cl(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (globaltimer() - t0 > kTimeoutNs) {
+    if (globaltimer() - t0 > limit) {
       *abort_flag = 1;
       return false;
     }
@@ -271,6 +273,11 @@ __device__ __forceinline__ void mma_f16_pair(uint32_t d_tmem, uint64_t adesc, ui
 __device__ __forceinline__ void mma_commit_pair(uint32_t cl_addr) {
   asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(cl_addr)
                : "memory");
+}
+
+// the bound of the kernel's mbarrier waits
+__device__ __forceinline__ unsigned long long wait_limit(const SqArgs& a) {
+  return a.wait_ns ? a.wait_ns : kTimeoutNs;
 }
 
 __device__ __forceinline__ LayerParams load_params(const SqArgs& a, int b) {

@@ -47,3 +47,27 @@ def test_n16384_sampled_parity_and_determinism(big):
     blk = D1[:512, -512:].cpu().numpy()
     blkT = D1[-512:, :512].cpu().numpy().T
     assert np.max(np.abs(blk - blkT)) <= 1e-6
+
+
+def test_n16384_whole_super_rows(big):
+    """Three complete 256-row blocks of D (the first, middle and last super
+    rows, all 16384 columns) against Q_occ Q_occ^T element by element.  Every
+    K block of these rows' products was read both ways (K-major right of the
+    diagonal, transposed from the stored upper block left of it), so a wrong
+    transposed read in any super-tile column shows up here."""
+    sp2, h = big
+    N, n_occ = h.N, h.n_occ
+    H = torch.from_numpy(h.h32()).cuda()
+    D, st = sp2.density_matrix(H, n_occ, precision="split")
+    assert st.status == 0
+    T = (N + 255) // 256
+    worst = 0.0
+    for I in (0, T // 2, T - 1):
+        rows = np.arange(I * 256, min(N, (I + 1) * 256))
+        want = o.density_matrix_closed_form(h.Q, n_occ, rows, None)
+        got = D[int(rows[0]): int(rows[-1]) + 1].cpu().numpy().astype(np.float64)
+        err = float(np.max(np.abs(got - want)))
+        worst = max(worst, err)
+        print(f"super row {I}: max_abs over {got.size} entries = {err:.3e}")
+        assert err <= 5e-5
+    print(f"N={N}: whole super rows worst max_abs = {worst:.3e}")

@@ -158,3 +158,62 @@ def test_adjoint_plain_fp16(sp2):
     print(f"adjoint fp16: dcoef rel {rel:.2e}, G0 rel {g0:.2e}")
     assert rel <= 1e-2
     assert g0 <= 1e-2
+
+
+def test_network_at_its_configuration(sp2):
+    """The network workload's shape (Eq. 16 in matrix form): N = 2048, L = 20,
+    checkpoints every 5 layers, coefficients at the SP2 branch values of
+    instance 0's FP64 solve (C15), the Fermi-Dirac target at kT = 0.05, mu = 0
+    (C14) and the squared Frobenius loss (C16); B = 4 instances keep the FP64
+    oracle affordable.  Checked: X_L and every checkpoint against the oracle's
+    forward; dcoef and dL/dX_0 of the hand-written adjoint against the
+    oracle's FP64 adjoint; and six coefficient gradients against central
+    differences (h = 1e-4) of the GPU forward with the loss summed in FP64.
+
+    Central differences of a forward that stores X in FP32 carry an absolute
+    noise floor: the two perturbed forwards round every element of every
+    layer differently, which moves the loss by ~1e-6 and the quotient by a few
+    1e-2 on gradients of up to ~2e2.  Their errors are therefore measured, as
+    the comparison with the oracle's adjoint is, against the largest
+    coefficient gradient."""
+    B, N, L, ce = 4, 2048, 20, 5
+    hs = [si.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), seed=2000 + i, device="cuda")
+          for i in range(B)]
+    r = o.sp2(hs[0].h32().astype(np.float64), hs[0].n_occ, max_iter=L, refine=False)
+    coef = o.sp2_branch_coefficients(r.sigmas, L).astype(np.float32)
+    H = torch.from_numpy(np.stack([h.h32() for h in hs])).cuda()
+    X, ck, _ = sp2.network_forward(H, coef, ckpt_every=ce)
+    X0 = _oracle_x0(hs)
+    XL, xs = o.network_forward(X0, coef.astype(np.float64), keep=True)
+    Xh = X.cpu().numpy().astype(np.float64)
+    fwd = float(np.max(np.abs(Xh - XL)))
+    ckerr = max(float(np.max(np.abs(ck[k].cpu().numpy() - xs[k * ce]))) for k in range(L // ce + 1))
+    del xs
+    target = np.stack([o.fermi_dirac_closed_form(h.Q, h.eps, 0.0, 0.05) for h in hs])
+    G_L = (2.0 * (Xh - target) / B).astype(np.float32)
+    dcoef, G0 = sp2.network_backward(H, coef, ce, ck, torch.from_numpy(G_L).cuda())
+    want_d, want_G0 = o.network_adjoint(X0, coef.astype(np.float64), G_L.astype(np.float64))
+    d = dcoef.numpy().astype(np.float64)
+    rel_d = float(np.max(np.abs(d - want_d)) / np.max(np.abs(want_d)))
+    rel_g0 = float(np.max(np.abs(G0.cpu().numpy() - want_G0)) / np.max(np.abs(want_G0)))
+
+    T = torch.from_numpy(target).cuda()
+
+    def loss(cf):
+        Xc, _, _ = sp2.network_forward(H, cf, ckpt_every=ce)
+        return float(((Xc.double() - T) ** 2).sum().item() / B)
+
+    fd_err = 0.0
+    for n, k in [(0, 0), (0, 1), (4, 2), (9, 0), (14, 1), (19, 2)]:
+        cp, cm = coef.copy(), coef.copy()
+        cp[n, k] = np.float32(coef[n, k] + 1e-4)
+        cm[n, k] = np.float32(coef[n, k] - 1e-4)
+        fd = (loss(cp) - loss(cm)) / (float(cp[n, k]) - float(cm[n, k]))
+        e = abs(fd - d[n, k]) / np.max(np.abs(d))
+        print(f"  coef ({n},{k}): adjoint {d[n, k]:+.6e}  central difference {fd:+.6e}  rel {e:.2e}")
+        fd_err = max(fd_err, e)
+    print(f"network B={B} N={N} L={L}: forward max-abs {fwd:.2e}, checkpoints {ckerr:.2e}; "
+          f"adjoint vs FP64 adjoint: dcoef rel {rel_d:.2e}, G0 rel {rel_g0:.2e}; vs central differences {fd_err:.2e}")
+    assert fwd <= 1e-4 and ckerr <= 1e-4
+    assert rel_d <= 1e-3 and rel_g0 <= 1e-3
+    assert fd_err <= 1e-3

@@ -78,3 +78,47 @@ def test_fit_matches_fermi_dirac_with_eleven_layers():
     for a, b, cc in theta:
         e = a * e * e + b * e + cc
         assert np.max(np.abs(e)) < 4.0
+
+
+# --- pins of the target function itself, F(eps) = 1/(exp(beta (eps - 1/2)) + 1)
+# (Eq. 19).  Each one is a property of the logistic step that a dropped beta,
+# a flipped sign of (eps - 1/2) or a wrong centre fails.
+
+def test_fermi_scaled_is_one_half_at_the_centre():
+    for beta in (1.0, 40.0, 880.0):
+        assert o.fermi_dirac_scaled(0.5, beta) == 0.5
+
+
+def test_fermi_scaled_value_where_the_exponential_is_three():
+    # at eps = 1/2 + ln(3)/beta the exponential equals 3, so F = 1/4; the
+    # mirrored point gets 3/4 (a sign error swaps them, a missing beta gives ~0.49)
+    beta = 40.0
+    x = 0.5 + np.log(3.0) / beta
+    assert abs(o.fermi_dirac_scaled(x, beta) - 0.25) <= 1e-15
+    assert abs(o.fermi_dirac_scaled(1.0 - x, beta) - 0.75) <= 1e-15
+
+
+def test_fermi_scaled_particle_hole_symmetry_and_monotone():
+    e = np.linspace(0.0, 1.0, 1001)
+    f = o.fermi_dirac_scaled(e, 40.0)
+    assert np.max(np.abs(f + o.fermi_dirac_scaled(1.0 - e, 40.0) - 1.0)) <= 1e-15
+    assert np.all(np.diff(f) < 0.0)             # occupied below the centre, empty above
+    assert f[0] > 1.0 - 1e-8 and f[-1] < 1e-8  # e^(-20) ~ 2e-9 from the integers
+
+
+def test_fermi_scaled_slope_at_the_centre():
+    # dF/deps at 1/2 is -beta/4 (derivative of the logistic at its midpoint)
+    beta, h = 40.0, 1e-6
+    d = (o.fermi_dirac_scaled(0.5 + h, beta) - o.fermi_dirac_scaled(0.5 - h, beta)) / (2 * h)
+    assert abs(d + beta / 4.0) <= 1e-6 * beta
+
+
+def test_fermi_scaled_is_fermi_dirac_on_the_mapped_axis():
+    """Q diag(F((E - e_lo)/(e_hi - e_lo))) Q^T equals the Fermi-Dirac matrix
+    (Eqs. 1, 5) with kT = (e_hi - e_lo)/beta and mu = (e_lo + e_hi)/2."""
+    h = si.gapped_hamiltonian(48, 24, (-1.0, -0.1), (0.1, 1.0), seed=5)
+    e_lo, e_hi, beta = -1.3, 1.1, 40.0
+    scaled = (h.eps - e_lo) / (e_hi - e_lo)
+    D1 = (h.Q * o.fermi_dirac_scaled(scaled, beta)) @ h.Q.T
+    D2 = o.fermi_dirac_closed_form(h.Q, h.eps, 0.5 * (e_lo + e_hi), (e_hi - e_lo) / beta)
+    assert np.max(np.abs(D1 - D2)) <= 1e-13
