@@ -63,7 +63,7 @@ enum BufId {
   B_HI0, B_LO0, B_HI1, B_LO1, B_Y0, B_Y1, B_CTL, B_TILES, B_TOFF, B_TCNT, B_TPART, B_IDONE,
   B_PART, B_TICKET, B_ERR, B_DPTR, B_NS, B_HS, B_TRACES, B_PARAMS, B_BOUNDS, B_RN, B_PART2,
   B_G, B_SEG, B_GH0, B_GL0, B_GH1, B_GL1, B_DOTS, B_TDOTS, B_PARAMS2, B_NALPHA, B_HP0, B_HP1, B_RNP0, B_RNP1,
-  B_READOUT, B_RDIAG, B_SEGP, B_COUNT
+  B_READOUT, B_RDIAG, B_SEGP, B_WAVE, B_COUNT
 };
 
 struct Buf {
@@ -107,6 +107,12 @@ struct State {
   bool fault_alloc = false, fault_nan = false, fault_stall = false;
   // side of the square groups of the tile order (SP2_TILE_GROUP, default 8)
   int tile_group = 8;
+  // K stages per epoch of the soft pair synchronisation (SP2_WAVE_SYNC, default
+  // 16; 0 = off)
+  int wave_sync = 16;
+  // with the synchronisation: K walked backwards on alternate waves
+  // (SP2_SNAKE=1; off by default)
+  int snake = 0;
   unsigned long long wait_ns = 0;  // bound of the squaring kernels' waits (0: 4 s)
 };
 
@@ -452,6 +458,10 @@ sp2_status sp2_init(const sp2_config* cfg) {
     g.batched_sched = (bk && strcmp(bk, "single") == 0) ? 1 : (bk && strcmp(bk, "pairs") == 0) ? 2 : 0;
     const char* gv = getenv("SP2_GRAPHS");
     g.use_graphs = !(gv && strcmp(gv, "0") == 0);
+    const char* wsy = getenv("SP2_WAVE_SYNC");
+    g.wave_sync = wsy ? std::max(0, std::min(4096, atoi(wsy))) : 16;
+    const char* sn = getenv("SP2_SNAKE");
+    g.snake = (sn && strcmp(sn, "1") == 0) ? 1 : 0;
     const char* tg = getenv("SP2_TILE_GROUP");
     const int tgv = tg ? atoi(tg) : 8;
     if (tgv != g.tile_group) g.tiles_key_N = -1;
@@ -788,8 +798,22 @@ sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int
     A.fused_ctl = 1;
     A.tri_y = 1;  // between launches only the upper triangle of Y' is kept
     A.tri_planes = g.pair_kernel ? 1 : 0;  // and of the planes, where the kernel reads them so
+    // epoch counters of the soft pair synchronisation, one zeroed slice per launch
+    unsigned* wave = nullptr;
+    size_t wave_per_launch = 0;
+    if (g.pair_kernel && g.wave_sync > 0) {
+      const int ncl = grid / 2, nsuper = ntiles / 2;
+      const long long stages = (long long)((nsuper + ncl - 1) / ncl) * ((N + 63) / 64);
+      wave_per_launch = (size_t)(stages / g.wave_sync + 2);
+      void* wv;
+      CKS(ws(B_WAVE, wave_per_launch * nlaunch * sizeof(unsigned), &wv, true));
+      wave = (unsigned*)wv;
+      A.sync_stages = g.wave_sync;
+      A.snake = g.snake;
+    }
     CK(cudaEventRecord(g.lev[0], st));
     for (int k = 0; k < nlaunch; ++k) {
+      A.wave_ctr = wave ? wave + (size_t)k * wave_per_launch : nullptr;
       const int cur = k & 1;
       A.hi_out = (__half*)hi[cur ^ 1];
       A.lo_out = (__half*)lo[cur ^ 1];

@@ -74,6 +74,17 @@ struct SqArgs {
   unsigned long long wait_ns;  // bound of every mbarrier wait of the tcgen05 kernels (0: 4 s)
   int stall;               // fault injection: the MMA issuer first waits on a barrier that
                            // nothing arrives on, so that wait runs out after wait_ns
+  // Soft synchronisation of the CTA pairs' K progress (CTA-pair kernel, one
+  // instance): every sync_stages K stages a pair publishes the epoch it
+  // finished in wave_ctr[epoch] and, before loading further, waits (bounded;
+  // it stops waiting for the rest of the launch after one time-out) until
+  // every pair has finished the epoch before that one.  Pairs that share an
+  // operand panel then read it within a short time of each other, while it
+  // is still in L2.  wave_ctr: zeroed counters of this launch; nullptr = off.
+  unsigned* wave_ctr;
+  int sync_stages;
+  int snake;               // 1: a pair walks K backwards on its odd-numbered tiles, so that a
+                           //    wave starts on the K slices the previous wave left in L2
 };
 
 // tensor-core tile geometry

@@ -92,6 +92,30 @@ __device__ __forceinline__ void load_half(uint8_t* dst, const CUtensorMap* tmK, 
   }
 }
 
+// Number of pairs with at least one K stage in epoch e (W stages each) when
+// pair c takes super tiles c, c + ncl, ... of nsuper, each of nk stages (one
+// instance, every tile active).
+__device__ __forceinline__ unsigned pairs_in_epoch(uint32_t e, int W, int nk, int nsuper, int ncl) {
+  const long long first = (long long)e * W;  // first stage of the epoch
+  const int q = nsuper / ncl, r = nsuper % ncl;
+  if (first < (long long)q * nk) return (unsigned)min(ncl, nsuper);
+  if (first < (long long)(q + 1) * nk) return (unsigned)r;
+  return 0u;
+}
+
+// Waits until *ctr >= need; false (stop waiting for the rest of the launch)
+// once the wait has taken longer than a small fraction of the wait bound.
+__device__ __forceinline__ bool epoch_wait(const unsigned* ctr, unsigned need, unsigned long long lim) {
+  const volatile unsigned* c = ctr;
+  if (*c >= need) return true;
+  const unsigned long long give_up = lim / 16 < 250000ull ? lim / 16 : 250000ull;  // <= 250 us
+  const uint64_t t0 = globaltimer();
+  while (*c < need) {
+    if (globaltimer() - t0 > give_up) return false;
+  }
+  return true;
+}
+
 // RO: readout mode of the epilogue (finite-temperature expansion).
 // tm_p0A/p1A: planes with 64 x 128 boxes (the A half); tm_p0B/p1B: the same
 // boxes for the B half; tm_p0T / tm_p1T: 64 x 64 boxes (transposed reads).
@@ -163,6 +187,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t armed[STAGES];
 #pragma unroll
       for (int s = 0; s < STAGES; ++s) armed[s] = 0;
+      // soft synchronisation of the pairs (even CTA): gs counts this pair's K
+      // stages over the launch, an epoch is W of them
+      const int W = a.sync_stages;
+      bool wait_sync = rank == 0 && a.wave_ctr != nullptr && W > 0;
+      const bool pub_sync = wait_sync;
+      uint32_t gs = 0;
       for (int u = cl; u < nsuper && ok; u += ncl) {
         int b, I, J, h;
         unpack_tile(a.tiles[2 * u + (int)rank], b, I, J, h);
@@ -170,7 +200,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int N = a.Ns[b];
         const int rowA = I * BN + (int)rank * BH, rowB = J * BN + (int)rank * BH;
         const int nk = (N + BK - 1) / BK;
-        for (int kb = 0; kb < nk; ++kb) {
+        const bool rev = a.snake && (((u - cl) / ncl) & 1);
+        for (int kk = 0; kk < nk; ++kk, ++gs) {
+          const int kb = rev ? nk - 1 - kk : kk;
+          if (pub_sync && gs > 0 && gs % (uint32_t)W == 0) {
+            const uint32_t e = gs / (uint32_t)W - 1u;  // the epoch this pair just finished
+            atomicAdd(&a.wave_ctr[e], 1u);
+            if (wait_sync && e >= 1u)
+              wait_sync = epoch_wait(a.wave_ctr + (e - 1u), pairs_in_epoch(e - 1u, W, nk, nsuper, ncl), lim);
+          }
           if (!mbar_wait_cl(&empty[stage], phase ^ 1u, abort_flag, lim)) {
             ok = false;
             break;
@@ -198,6 +236,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
       }
+      // the last (possibly partial) epoch of this pair
+      if (pub_sync && gs > 0) atomicAdd(&a.wave_ctr[(gs - 1u) / (uint32_t)W], 1u);
       if (!ok || *abort_flag) {
         atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
         st_cluster_u32(peer_abort, 1u);
@@ -236,6 +276,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!load_params(a, b).active) continue;
         const int N = a.Ns[b];
         const int nk = (N + BK - 1) / BK;
+        const bool rev = a.snake && (((u - cl) / ncl) & 1);
         const uint32_t buf = it & 1u;
         (void)h;
         // the k-th use of a buffer waits for the epilogues' (k-1)-th release
@@ -245,7 +286,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         tc_fence_after();
         const uint32_t d = tmem_base + buf * BN;
-        for (int kb = 0; kb < nk; ++kb) {
+        for (int kk = 0; kk < nk; ++kk) {
+          const int kb = rev ? nk - 1 - kk : kk;
           if (!mbar_wait_cl(&full[stage], phase, abort_flag, lim)) {
             ok = false;
             break;
@@ -261,7 +303,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             // K step ks: 32 B along a K-major row, or two 8-row K groups
             const uint32_t oa = ta ? ks * 2048u : ks * UMMA_K * 2u;
             const uint32_t ob = tb ? ks * 2048u : ks * UMMA_K * 2u;
-            const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
+            const uint32_t acc = (kk > 0 || ks > 0) ? 1u : 0u;
             if (SPLIT) {
               const uint64_t dhpA = ta ? make_desc_mn128(st + OFF_HPA + oa) : make_desc_sw128(st + OFF_HPA + oa);
               const uint64_t dloA = ta ? make_desc_mn128(st + OFF_LOA + oa) : make_desc_sw128(st + OFF_LOA + oa);
