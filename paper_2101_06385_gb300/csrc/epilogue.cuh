@@ -12,7 +12,11 @@
 //
 // Warp ew (0..7) owns TMEM lane quarter q (the warp's index mod 4, a
 // hardware rule) and column half ew / 4: 32 rows x 128 columns, drained in
-// four 32-column chunks (tcgen05.ld 32x32b: one row per lane).
+// four 32-column chunks (tcgen05.ld 32x32b: one row per lane).  Each chunk is
+// turned through a 4 KB shared-memory buffer of the warp so that a lane holds
+// four consecutive columns of eight rows: the loads and stores of the
+// iterate, the planes and the other row-major operands then cover whole
+// 128-byte row segments.
 //
 // No named barrier is used: the eight per-warp partials of a tile meet in
 // shared memory and the last warp to arrive (shared atomic counter) sums
@@ -74,27 +78,6 @@ __device__ __forceinline__ double row_norm(const SqArgs& a, int b, int N, int r)
   return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
-// Lane L returns sum over the 32 lanes of y[L]^2 (lanes with valid == false
-// contribute zero): a butterfly that halves the values held per lane at each
-// of the five exchange steps (31 shuffles).
-__device__ __forceinline__ float column_sums_sq(const float (&y)[32], bool valid) {
-  const int lane = threadIdx.x & 31;
-  float s[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) s[j] = valid ? y[j] * y[j] : 0.f;
-#pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
-    const bool upper = (lane & w) != 0;
-#pragma unroll
-    for (int k = 0; k < w; ++k) {
-      const float send = upper ? s[k] : s[k + w];
-      const float keep = upper ? s[k + w] : s[k];
-      s[k] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-    }
-  }
-  return s[0];
-}
-
 // Release of accumulator buffer buf by one lane of an epilogue warp.
 template <bool PAIR>
 __device__ __forceinline__ void release(uint64_t* tmem_empty, uint32_t buf, uint32_t empty_cl) {
@@ -102,6 +85,61 @@ __device__ __forceinline__ void release(uint64_t* tmem_empty, uint32_t buf, uint
     sp2::tc::mbar_arrive_cl(empty_cl + 8u * buf);
   else
     sp2::tc::mbar_arrive(&tmem_empty[buf]);
+}
+
+// The warp's staging buffer in shared memory holds one 32 x 32 FP32 chunk,
+// row r at r * 32 floats, its 16-byte group m (columns 4m .. 4m + 3) at group
+// m ^ (r & 7).  A warp writing one row per lane, or reading four rows with
+// eight lanes each, touches every bank once per 128 bytes: four wavefronts
+// per 512-byte access, the least there can be.
+constexpr int TR_FLOATS = 32 * 32;
+constexpr int TR_BYTES = WARPS * TR_FLOATS * 4;  // per CTA: 32 KB
+
+__device__ __forceinline__ float4* tr_at(float* trb, int r, int m) {
+  return reinterpret_cast<float4*>(trb + r * 32 + ((m ^ (r & 7)) << 2));
+}
+
+// Four consecutive floats of a row, columns c .. c + 3 at p (zeros at and
+// past column n); one 16-byte access when vec (16-byte aligned rows) and the
+// four are inside.
+__device__ __forceinline__ float4 ld4(const float* p, int c, int n, bool vec) {
+  if (vec && c + 4 <= n) return *reinterpret_cast<const float4*>(p);
+  float4 r;
+  r.x = c < n ? p[0] : 0.f;
+  r.y = c + 1 < n ? p[1] : 0.f;
+  r.z = c + 2 < n ? p[2] : 0.f;
+  r.w = c + 3 < n ? p[3] : 0.f;
+  return r;
+}
+__device__ __forceinline__ void st4(float* p, float4 v, int c, int n, bool vec) {
+  if (vec && c + 4 <= n) {
+    *reinterpret_cast<float4*>(p) = v;
+    return;
+  }
+  if (c < n) p[0] = v.x;
+  if (c + 1 < n) p[1] = v.y;
+  if (c + 2 < n) p[2] = v.z;
+  if (c + 3 < n) p[3] = v.w;
+}
+
+// Sums over the N_ lanes that differ only in lane bits LOWBIT .. LOWBIT +
+// log2(N_) - 1: each of them holds N_ values s[0 .. N_), and a lane returns
+// the total over those lanes of value index (lane >> LOWBIT) & (N_ - 1).  A
+// halving butterfly (N_ - 1 shuffles); s is overwritten.
+template <int N_, int LOWBIT>
+__device__ __forceinline__ float lane_sums(float (&s)[N_]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int w = N_ / 2; w >= 1; w >>= 1) {
+    const bool upper = ((lane >> LOWBIT) & w) != 0;
+#pragma unroll
+    for (int k = 0; k < w; ++k) {
+      const float send = upper ? s[k] : s[k + w];
+      const float keep = upper ? s[k + w] : s[k];
+      s[k] = keep + __shfl_xor_sync(0xffffffffu, send, w << LOWBIT);
+    }
+  }
+  return s[0];
 }
 
 // Tile t with accumulator use `it` (buffer it & 1).  Returns 0 when the
@@ -115,10 +153,19 @@ __device__ __forceinline__ void release(uint64_t* tmem_empty, uint32_t buf, uint
 // PAIR (CTA-pair kernels): the accumulator was written by the pair's MMA
 // issuer in the even CTA, and the release of a buffer is an arrive on that
 // CTA's barrier, empty_cl + 8 x buffer (a shared::cluster address).
+//
+// Layout of the work: a chunk is the warp's 32 accumulator rows x 32 columns
+// (lane = row after tcgen05.ld).  Through the staging buffer trb, lane
+// (r4, c4) = (lane / 8, lane % 8) takes columns c0 + 4 c4 .. + 3 of the
+// eight rows R0 + 4 i + r4 (registers 4 i .. 4 i + 3).  Every warp
+// instruction that loads or stores the iterate, the operand planes, H, R or
+// aux then covers four whole 128-byte row segments.  Stores of the mirror
+// block go back through the buffer to the row-per-lane layout, where they
+// are contiguous too.
 template <bool SPLIT, bool ADJ = false, bool RO = false, bool PAIR = false>
 __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_t tmem_base, uint64_t* tmem_full,
                                     uint64_t* tmem_empty, volatile int* abort_flag, Shared& sh, int ew, int q,
-                                    int lane, uint32_t empty_cl = 0u) {
+                                    int lane, float* trb, uint32_t empty_cl = 0u) {
   using namespace sp2::tc;
   int b, I, J, h;
   unpack_tile(a.tiles[t], b, I, J, h);
@@ -126,7 +173,8 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
   if (!p.active) return 0;
   const int N = a.Ns[b];
   const int hc = ew >> 2;
-  const int r = I * BN + h * BM + q * 32 + lane;
+  const int R0 = I * BN + h * BM + q * 32;  // first of the warp's 32 rows
+  const int nrows = min(32, N - R0);        // rows of the warp inside the matrix (may be <= 0)
   const bool mirror = (I != J);
   const bool outD = (p.out_mode == OUT_D);
   // split: the accumulator holds 2^(2s) P (both operand planes scaled by 2^s)
@@ -135,17 +183,21 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
   float* Y = a.Yout + (long long)b * a.slot_y;
   const float* Yold = a.Yin + (long long)b * a.slot_y;
   const long long ld = a.ld_y;
+  const int cbase = J * BN + hc * 128;      // first column of the warp's half
+  const int r4 = lane >> 3, c4 = lane & 7;
 
-  // issued before the accumulator wait: the diagonal's FP64 row norm and
-  // the old row segment (into L2)
-  double rn_r = 0.0;
-  if (r < N) {
-    const int dcol = r - (J * BN + hc * 128);
-    if (!mirror && (unsigned)dcol < 128u) rn_r = row_norm(a, b, N, r);
+  // issued before the accumulator wait: the FP64 row norm of the diagonal
+  // element this lane will hold (row R0 + 4 c4 + r4, in the chunk whose first
+  // column is R0) and the warp's old rows (into L2)
+  double rn_l = 0.0;
+  const int rdiag = R0 + 4 * c4 + r4;
+  const bool dwarp = !mirror && (unsigned)(R0 - cbase) < 128u;  // the warp's columns hold its diagonal
+  if (dwarp && rdiag < N) rn_l = row_norm(a, b, N, rdiag);
+  if (lane < nrows) {
 #pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
-      const int c0 = J * BN + hc * 128 + ch * 32;
-      if (c0 < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(Yold + (long long)r * ld + c0));
+    for (int c = 0; c < 4; ++c) {
+      const int c0 = cbase + c * 32;
+      if (c0 < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(Yold + (long long)(R0 + lane) * ld + c0));
     }
   }
 
@@ -168,20 +220,32 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
   __half* const pa_out = SPLIT ? hp_ : ho;
   const long long ldh = a.ld_h;
   float* D = outD ? a.Dptr[b] : nullptr;
+  // 16-byte accesses where every row start of the matrix is 16-byte aligned:
+  // Y, Y_old (and R, aux) with leading dimension ld; D and H with N
+  const float* Rb0 = RO ? a.R + (long long)b * a.slot_y : nullptr;
+  const float* Xb0 = ADJ ? a.aux + (long long)b * a.slot_y : nullptr;
+  const bool vec_y = (ld & 3) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(Yold) |
+                       reinterpret_cast<uintptr_t>(Rb0) | reinterpret_cast<uintptr_t>(Xb0)) & 15) == 0;
+  const float* Hb0 = (outD && !ADJ && a.Hobs) ? a.Hobs[b] : nullptr;
+  const bool vec_n = (N & 3) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(D) | reinterpret_cast<uintptr_t>(Hb0)) & 15) == 0;
   double tr = 0.0, sq = 0.0;
   // adjoint-mode dots; dtr carries the Tr[D A] partial in the launch that writes D
   double dtr = 0.0, dgy = 0.0, dpy = 0.0;
   const uint32_t taddr = tmem_base + buf * BN + ((uint32_t)(q * 32) << 16) + hc * 128;
-  const bool vec_y = (ld & 3) == 0;
 
   // chunks wholly past the padded K extent (columns >= round_up(N, 64)) or
   // warps whose 32 rows all lie past N have nothing to write (warp-uniform)
   const int kpad = (N + 63) & ~63;
-  const bool rows_live = I * BN + h * BM + q * 32 < N;
+  const bool rows_live = nrows > 0;
+  // mirror blocks stored in this launch (off-diagonal tiles only)
+  const bool mir_y = mirror && (outD || !a.tri_y);
+  const bool mir_p = mirror && !outD && !a.tri_planes && (pa_out || lo_);
 
 #pragma unroll 1
   for (int ch = 0; ch < 4; ++ch) {
-    const int c0 = J * BN + hc * 128 + ch * 32;
+    const int c0 = cbase + ch * 32;
     if (!rows_live || c0 >= kpad) {
       if (ch == 3) {
         tc_fence_before();
@@ -190,250 +254,248 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       }
       continue;
     }
-    // the diagonal element of row r, if it lies in this chunk (I == J only)
-    const int jd = r - c0;
-    const bool dchunk = !mirror && (unsigned)jd < 32u;
-    const bool full_chunk = (c0 + 32 <= N) && vec_y;
+    const int ce = c0 + 4 * c4;  // this lane's first column
+    // the one diagonal element a lane holds (chunk c0 == R0 of a diagonal
+    // tile): row = column = rdiag, register 4 c4 + r4
+    const bool dlane = !mirror && c0 == R0 && rdiag < N;
+    const int id = 4 * c4 + r4;
     // old values first: their global-load latency overlaps the TMEM load
     float y[32];
-    if (r >= N) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) y[j] = 0.f;
-    } else if (full_chunk) {
-      const float4* src = reinterpret_cast<const float4*>(Yold + (long long)r * ld + c0);
+    for (int i = 0; i < 8; ++i) {
+      const bool rok = 4 * i + r4 < nrows;
+      const float4 o = rok ? ld4(Yold + (long long)(R0 + 4 * i + r4) * ld + ce, ce, N, vec_y)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+      y[4 * i] = o.x;
+      y[4 * i + 1] = o.y;
+      y[4 * i + 2] = o.z;
+      y[4 * i + 3] = o.w;
+    }
+    {
+      uint32_t v[32];
+      __syncwarp();
+      tmem_ld32(taddr + ch * 32, v);
+      tmem_ld_wait();
+      if (ch == 3) {
+        // accumulator drained: the MMA issuer may reuse this buffer
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) release<PAIR>(tmem_empty, buf, empty_cl);
+      }
+      // lane = row -> lane = (four rows, four columns)
 #pragma unroll
-      for (int j4 = 0; j4 < 8; ++j4) {
-        const float4 o = src[j4];
-        y[4 * j4 + 0] = o.x;
-        y[4 * j4 + 1] = o.y;
-        y[4 * j4 + 2] = o.z;
-        y[4 * j4 + 3] = o.w;
+      for (int m = 0; m < 8; ++m)
+        *tr_at(trb, lane, m) = make_float4(__uint_as_float(v[4 * m]), __uint_as_float(v[4 * m + 1]),
+                                           __uint_as_float(v[4 * m + 2]), __uint_as_float(v[4 * m + 3]));
+    }
+    __syncwarp();
+    float yold_d = 0.f, p_d = 0.f;
+    {
+      float gy = 0.f, py = 0.f;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float4 pv = *tr_at(trb, 4 * i + r4, c4);
+        const float P[4] = {pv.x * unscale, pv.y * unscale, pv.z * unscale, pv.w * unscale};
+        const bool rok = 4 * i + r4 < nrows;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        if (ADJ && rok) {
+          const float4 xv = ld4(a.aux + (long long)b * a.slot_y + (long long)(R0 + 4 * i + r4) * ld + ce, ce, N, vec_y);
+          x[0] = xv.x;
+          x[1] = xv.y;
+          x[2] = xv.z;
+          x[3] = xv.w;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = 4 * i + e;
+          if (ADJ) {
+            // dots on the old values (before the update overwrites y)
+            gy = fmaf(y[k], x[e], gy);
+            py = fmaf(P[e], x[e], py);
+          }
+          if (dlane && k == id) {
+            yold_d = y[k];
+            p_d = P[e];
+          }
+          const float yn = fmaf(p.ca, y[k], p.cb * P[e]);
+          y[k] = (rok && ce + e < N) ? yn : 0.f;
+        }
+      }
+      if (ADJ) {
+        dgy += (double)gy;
+        dpy += (double)py;
+        if (dlane) dtr += (double)yold_d;
+      }
+    }
+    __syncwarp();
+    // one FP64 update per diagonal element, outside the unrolled element loop
+    float ydo = 0.f;
+    double yd = 0.0;
+    if (dlane) {
+      const double pd = (a.rn || a.rnp_in) ? rn_l : (double)p_d;
+      yd = p.ca_d * (double)yold_d + p.cb_d * pd + p.cc_d;
+      tr += yd;
+      const float ydf = (float)yd;
+      ydo = outD ? (float)(yd + p.alpha_out) : ydf;
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if (k == id) y[k] = ydf;
+    }
+    // sums of squares of Y': per row (over the chunk's 32 columns) and per
+    // column (over the warp's 32 rows), and this lane's share of ||Y'||_F^2
+    float rs[8], cs[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      rs[i] = 0.f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float s2 = y[4 * i + e] * y[4 * i + e];
+        rs[i] += s2;
+        cs[e] += s2;
+      }
+    }
+    sq += (double)(((rs[0] + rs[1]) + (rs[2] + rs[3])) + ((rs[4] + rs[5]) + (rs[6] + rs[7])));
+    if (rnp) {
+      // row R0 + 4 c4 + r4, segment c0 / 32; and for the mirror, row
+      // c0 + 4 c4 + r4 (a column here), segment R0 / 32
+      const float rsum = lane_sums<8, 0>(rs);
+      if (rdiag < N && c0 < N) rnp[(long long)(c0 >> 5) * a.ld_rnp + rdiag] = rsum;
+      if (mirror) {
+        const float csum = lane_sums<4, 3>(cs);
+        const int cm = c0 + 4 * c4 + r4;
+        if (cm < N) rnp[(long long)(R0 >> 5) * a.ld_rnp + cm] = csum;
+      }
+    }
+    if (RO) {
+      // readout R += rc X' over the upper tiles (R is symmetric; its lower
+      // half is only needed as D, written with the mirror below); all loads
+      // before the first store (the compiler cannot tell the rows apart)
+      // (rows in two halves of four, to bound the registers held)
+      float* Rb = a.R + (long long)b * a.slot_y + (long long)R0 * ld + ce;
+      double rd = 0.0;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        float4 rv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = 4 * hh + u;
+          rv[u] = (4 * i + r4 < nrows) ? ld4(Rb + (long long)(4 * i + r4) * ld, ce, N, vec_y)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // register id = 4 c4 + r4: row group c4, component r4
+        if (dlane && (c4 >> 2) == hh) {
+          float rold = 0.f;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (4 * hh + u == c4) rold = r4 == 0 ? rv[u].x : r4 == 1 ? rv[u].y : r4 == 2 ? rv[u].z : rv[u].w;
+          rd = (double)rold + p.rc_d * (yd + p.alpha_new);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = 4 * hh + u;
+          const bool rok = 4 * i + r4 < nrows;
+          float r_[4] = {rv[u].x, rv[u].y, rv[u].z, rv[u].w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = 4 * i + e;
+            r_[e] = fmaf(p.rc, y[k], r_[e]);
+            if (dlane && k == id) r_[e] = (float)rd;
+            if (outD) y[k] = (rok && ce + e < N) ? -r_[e] : 0.f;  // D = I - R
+          }
+          if (!outD && rok)
+            st4(Rb + (long long)(4 * i + r4) * ld, make_float4(r_[0], r_[1], r_[2], r_[3]), ce, N, vec_y);
+        }
+      }
+      if (outD) ydo = (float)(1.0 - rd);
+    }
+    if (outD) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (4 * i + r4 < nrows) {
+          float d_[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) d_[e] = (dlane && 4 * i + e == id) ? ydo : y[4 * i + e];
+          st4(D + (long long)(R0 + 4 * i + r4) * N + ce, make_float4(d_[0], d_[1], d_[2], d_[3]), ce, N, vec_n);
+        }
+      }
+      if (!ADJ && a.Hobs) {
+        // Tr[D A] over this chunk (A symmetric: the mirror counts twice below)
+        float eo = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (4 * i + r4 < nrows) {
+            const float4 hv = ld4(a.Hobs[b] + (long long)(R0 + 4 * i + r4) * N + ce, ce, N, vec_n);
+            const float hx[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) eo = fmaf((dlane && 4 * i + e == id) ? ydo : y[4 * i + e], hx[e], eo);
+          }
+        }
+        dtr += (double)eo;
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) y[j] = (c0 + j < N) ? Yold[(long long)r * ld + c0 + j] : 0.f;
+      for (int i = 0; i < 8; ++i)
+        if (4 * i + r4 < nrows)
+          st4(Y + (long long)(R0 + 4 * i + r4) * ld + ce, make_float4(y[4 * i], y[4 * i + 1], y[4 * i + 2], y[4 * i + 3]),
+              ce, N, vec_y);
     }
-    uint32_t v[32];
-    const bool packs = !outD && r < N && (pa_out || lo_) && c0 + 32 <= (int)ldh;
-    __syncwarp();
-    tmem_ld32(taddr + ch * 32, v);
-    tmem_ld_wait();
-    if (ch == 3) {
-      // accumulator drained: the MMA issuer may reuse this buffer
-      tc_fence_before();
+    // FP16 planes of Y' (Eq. 12): the row segments, four halves per plane and
+    // lane (columns up to the padded row length carry zeros)
+    if (!outD && (pa_out || lo_) && c0 + 32 <= (int)ldh) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (4 * i + r4 < nrows) {
+          uint32_t pa[2], pl[2];
+#pragma unroll
+          for (int e2 = 0; e2 < 2; ++e2) {
+            __half h0, l0, h1, l1;
+            split_fp16(y[4 * i + 2 * e2], lo_scale, h0, l0);
+            split_fp16(y[4 * i + 2 * e2 + 1], lo_scale, h1, l1);
+            pa[e2] = SPLIT ? pack_h2(__float2half_rn(__half2float(h0) * lo_scale),
+                                     __float2half_rn(__half2float(h1) * lo_scale))
+                           : pack_h2(h0, h1);
+            pl[e2] = pack_h2(l0, l1);
+          }
+          const long long off = (long long)(R0 + 4 * i + r4) * ldh + ce;
+          if (pa_out) *reinterpret_cast<uint2*>(pa_out + off) = make_uint2(pa[0], pa[1]);
+          if (lo_) *reinterpret_cast<uint2*>(lo_ + off) = make_uint2(pl[0], pl[1]);
+        }
+      }
+    }
+    if (mir_y || mir_p) {
+      // back to lane = row: lane L holds (row R0 + L, column c0 + k) in y[k],
+      // and the mirror element (c0 + k, R0 + L) is contiguous across lanes
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        *tr_at(trb, 4 * i + r4, c4) = make_float4(y[4 * i], y[4 * i + 1], y[4 * i + 2], y[4 * i + 3]);
       __syncwarp();
-      if (lane == 0) release<PAIR>(tmem_empty, buf, empty_cl);
-    }
-    if (r < N) {
-      float yold_d = 0.f, p_d = 0.f;
-      if (dchunk) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j == jd) {
-            yold_d = y[j];
-            p_d = __uint_as_float(v[j]) * unscale;
-          }
+      for (int m = 0; m < 8; ++m) {
+        const float4 o = *tr_at(trb, lane, m);
+        y[4 * m] = o.x;
+        y[4 * m + 1] = o.y;
+        y[4 * m + 2] = o.z;
+        y[4 * m + 3] = o.w;
       }
-      if (ADJ) {
-        // dots on the old values (before the update overwrites y)
-        const float* ax = a.aux + (long long)b * a.slot_y + (long long)r * ld + c0;
-        float gy = 0.f, py = 0.f;
+      __syncwarp();
+      if (lane < nrows) {
+        const int r = R0 + lane;
 #pragma unroll
-        for (int j4 = 0; j4 < 8; ++j4) {
-          float x[4];
-          if (full_chunk) {
-            const float4 o = reinterpret_cast<const float4*>(ax)[j4];
-            x[0] = o.x;
-            x[1] = o.y;
-            x[2] = o.z;
-            x[3] = o.w;
-          } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = (c0 + 4 * j4 + u < N) ? ax[4 * j4 + u] : 0.f;
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int j = 4 * j4 + u;
-            gy = fmaf(y[j], x[u], gy);
-            py = fmaf(__uint_as_float(v[j]) * unscale, x[u], py);
-          }
-        }
-        dgy += (double)gy;
-        dpy += (double)py;
-        if (dchunk) dtr += (double)yold_d;
-      }
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float P = __uint_as_float(v[j]) * unscale;
-        const float yn = fmaf(p.ca, y[j], p.cb * P);
-        y[j] = (c0 + j < N) ? yn : 0.f;
-      }
-      // one FP64 update per row, outside the unrolled element loop
-      float ydo = 0.f;
-      double yd = 0.0;
-      if (dchunk) {
-        const double pd = (a.rn || a.rnp_in) ? rn_r : (double)p_d;
-        yd = p.ca_d * (double)yold_d + p.cb_d * pd + p.cc_d;
-        tr += yd;
-        const float ydf = (float)yd;
-        ydo = outD ? (float)(yd + p.alpha_out) : ydf;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j == jd) y[j] = ydf;
-      }
-      float sqf = 0.f;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) sqf = fmaf(y[j], y[j], sqf);
-      sq += (double)sqf;
-      if (rnp && c0 < N) rnp[(long long)(c0 >> 5) * a.ld_rnp + r] = sqf;
-      if (RO) {
-        // readout R += rc X' over the upper tiles (R is symmetric; its lower
-        // half is only needed as D, written with the mirror below); two
-        // halves of 16 columns keep the register footprint down
-        float* Rr = a.R + (long long)b * a.slot_y + (long long)r * ld + c0;
-        double rd = 0.0;
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          float rv[16];
-          if (full_chunk) {
-#pragma unroll
-            for (int j4 = 0; j4 < 4; ++j4) {
-              const float4 o = reinterpret_cast<const float4*>(Rr + 16 * hh)[j4];
-              rv[4 * j4 + 0] = o.x;
-              rv[4 * j4 + 1] = o.y;
-              rv[4 * j4 + 2] = o.z;
-              rv[4 * j4 + 3] = o.w;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) rv[j] = (c0 + 16 * hh + j < N) ? Rr[16 * hh + j] : 0.f;
-          }
-          const bool dhalf = dchunk && (jd >> 4) == hh;
-          if (dhalf) {
-            float rold = 0.f;
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (16 * hh + j == jd) rold = rv[j];
-            rd = (double)rold + p.rc_d * (yd + p.alpha_new);
-          }
-#pragma unroll
-          for (int j = 0; j < 16; ++j) rv[j] = fmaf(p.rc, y[16 * hh + j], rv[j]);
-          if (dhalf) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (16 * hh + j == jd) rv[j] = (float)rd;
-          }
-          if (outD) {
-            // D = I - R: the values the D stores (and the mirror) write
-#pragma unroll
-            for (int j = 0; j < 16; ++j) y[16 * hh + j] = (c0 + 16 * hh + j < N) ? -rv[j] : 0.f;
-          } else if (full_chunk) {
-#pragma unroll
-            for (int j4 = 0; j4 < 4; ++j4)
-              reinterpret_cast<float4*>(Rr + 16 * hh)[j4] =
-                  make_float4(rv[4 * j4], rv[4 * j4 + 1], rv[4 * j4 + 2], rv[4 * j4 + 3]);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (c0 + 16 * hh + j < N) Rr[16 * hh + j] = rv[j];
-          }
-        }
-        if (outD) ydo = (float)(1.0 - rd);
-      }
-      if (outD) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (c0 + j < N) D[(long long)r * N + c0 + j] = (dchunk && j == jd) ? ydo : y[j];
-        if (!ADJ && a.Hobs) {
-          // Tr[D A] over this row segment (A symmetric: the mirror counts twice below)
-          const float* hr = a.Hobs[b] + (long long)r * N + c0;
-          const bool hvec = ((N & 3) == 0) && (c0 + 32 <= N) && ((((uintptr_t)a.Hobs[b]) & 15) == 0);
-          float eo = 0.f;
-#pragma unroll
-          for (int j4 = 0; j4 < 8; ++j4) {
-            float x[4];
-            if (hvec) {
-              const float4 o = reinterpret_cast<const float4*>(hr)[j4];
-              x[0] = o.x;
-              x[1] = o.y;
-              x[2] = o.z;
-              x[3] = o.w;
-            } else {
-#pragma unroll
-              for (int u = 0; u < 4; ++u) x[u] = (c0 + 4 * j4 + u < N) ? hr[4 * j4 + u] : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int j = 4 * j4 + u;
-              eo = fmaf((dchunk && j == jd) ? ydo : y[j], x[u], eo);
-            }
-          }
-          dtr += (double)eo;
-        }
-      } else {
-        if (full_chunk) {
-          float4* dst = reinterpret_cast<float4*>(Y + (long long)r * ld + c0);
-#pragma unroll
-          for (int j4 = 0; j4 < 8; ++j4) dst[j4] = make_float4(y[4 * j4], y[4 * j4 + 1], y[4 * j4 + 2], y[4 * j4 + 3]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (c0 + j < N) Y[(long long)r * ld + c0 + j] = y[j];
-        }
-      }
-    }
-    // row norms of the mirror: rows c0 + j of Y' get the segment of the 32
-    // rows of this warp, the column sums of y^2 over the lanes
-    if (mirror && rnp) {
-      const float cs = column_sums_sq(y, r < N);
-      if (c0 + lane < N) rnp[(long long)((I * BN + h * BM + q * 32) >> 5) * a.ld_rnp + c0 + lane] = cs;
-    }
-    // mirrored store: lanes hold consecutive rows r -> consecutive columns
-    if (mirror && r < N && (outD || !a.tri_y)) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int c = c0 + j;
-        if (c < N) {
-          if (outD)
-            D[(long long)c * N + r] = y[j];
-          else
-            Y[(long long)c * ld + r] = y[j];
-        }
-      }
-    }
-    if (packs) {
-      // FP16 planes of Y': 32 halves per plane packed in registers, stored
-      // to the row segment and (off-diagonal tiles) its mirror; columns >= N
-      // carry zeros
-      uint32_t pa[16], pl[16];  // hp (split) or hi (plain), and lo'
-#pragma unroll
-      for (int j2 = 0; j2 < 16; ++j2) {
-        __half h0, l0, h1, l1;
-        split_fp16(y[2 * j2], lo_scale, h0, l0);
-        split_fp16(y[2 * j2 + 1], lo_scale, h1, l1);
-        pa[j2] = SPLIT ? pack_h2(__float2half_rn(__half2float(h0) * lo_scale),
-                                 __float2half_rn(__half2float(h1) * lo_scale))
-                       : pack_h2(h0, h1);
-        pl[j2] = pack_h2(l0, l1);
-      }
-      if (pa_out) {
-        uint4* dp = reinterpret_cast<uint4*>(pa_out + (long long)r * ldh + c0);
-#pragma unroll
-        for (int j4 = 0; j4 < 4; ++j4) dp[j4] = make_uint4(pa[4 * j4], pa[4 * j4 + 1], pa[4 * j4 + 2], pa[4 * j4 + 3]);
-      }
-      if (lo_) {
-        uint4* dl = reinterpret_cast<uint4*>(lo_ + (long long)r * ldh + c0);
-#pragma unroll
-        for (int j4 = 0; j4 < 4; ++j4) dl[j4] = make_uint4(pl[4 * j4], pl[4 * j4 + 1], pl[4 * j4 + 2], pl[4 * j4 + 3]);
-      }
-      if (mirror && !a.tri_planes) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int c = c0 + j;
+        for (int k = 0; k < 32; ++k) {
+          const int c = c0 + k;
           if (c < N) {
-            const int sh16 = 16 * (j & 1);
-            if (pa_out) pa_out[(long long)c * ldh + r] = __ushort_as_half((unsigned short)(pa[j >> 1] >> sh16));
-            if (lo_) lo_[(long long)c * ldh + r] = __ushort_as_half((unsigned short)(pl[j >> 1] >> sh16));
+            if (mir_y) {
+              if (outD)
+                D[(long long)c * N + r] = y[k];
+              else
+                Y[(long long)c * ld + r] = y[k];
+            }
+            if (mir_p) {
+              __half hh, ll;
+              split_fp16(y[k], lo_scale, hh, ll);
+              if (pa_out) pa_out[(long long)c * ldh + r] = SPLIT ? __float2half_rn(__half2float(hh) * lo_scale) : hh;
+              if (lo_) lo_[(long long)c * ldh + r] = ll;
+            }
           }
         }
       }

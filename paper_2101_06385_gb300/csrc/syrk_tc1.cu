@@ -47,6 +47,7 @@ constexpr int OFF_HPA = 0, OFF_LOA = A_BYTES, OFF_HPB = 2 * A_BYTES, OFF_LOB = 2
 // holds the second segment's operands) with the adjoint-mode epilogue: the
 // split SYR2K Y G + G Y of the network adjoint.
 template <bool SPLIT, bool NSEG2>
+
 __global__ void __launch_bounds__(THREADS, 1)
     syrk_tc1_kernel(const __grid_constant__ CUtensorMap tm_p0A, const __grid_constant__ CUtensorMap tm_p1A,
                     const __grid_constant__ CUtensorMap tm_p0B, const __grid_constant__ CUtensorMap tm_p1B,
@@ -66,6 +67,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* drain = tmem_empty + 2;
   uint64_t* never = drain + 1;  // fault injection: nothing arrives on it
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
+  // the epilogue warps' staging buffers, after the 256 bytes of barriers
+  float* trbuf = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256);
   __shared__ int s_abort;
   __shared__ epi::Shared s_epi;
 
@@ -221,7 +224,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t it = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
       const int rc =
-          epi::tile<SPLIT, NSEG2>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag, s_epi, ew, q, lane);
+          epi::tile<SPLIT, NSEG2>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag, s_epi, ew, q, lane,
+                                  trbuf + ew * epi::TR_FLOATS);
       if (rc < 0) break;
       it += (uint32_t)rc;
     }
@@ -257,7 +261,7 @@ cudaError_t set_smem_once(K kernel, int bytes, int which) {
 size_t syrk_tc1_smem_bytes(bool split) {
   const int stages = split ? tc1::STAGES_SPLIT : tc1::STAGES_PLAIN;
   const int sb = split ? tc1::STAGE_SPLIT : tc1::STAGE_PLAIN;
-  return (size_t)stages * sb + 1024 /* alignment slack */ + 256 /* barriers */;
+  return (size_t)stages * sb + 1024 /* alignment slack */ + 256 /* barriers */ + epi::TR_BYTES;
 }
 
 cudaError_t launch_syrk_tc1(const SqArgs& a, const CUtensorMap* tm, bool split, int grid, cudaStream_t st) {

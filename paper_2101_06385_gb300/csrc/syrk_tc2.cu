@@ -120,6 +120,7 @@ __device__ __forceinline__ bool epoch_wait(const unsigned* ctr, unsigned need, u
 // tm_p0A/p1A: planes with 64 x 128 boxes (the A half); tm_p0B/p1B: the same
 // boxes for the B half; tm_p0T / tm_p1T: 64 x 64 boxes (transposed reads).
 template <bool SPLIT, bool RO>
+
 __global__ void __launch_bounds__(THREADS, 1)
     syrk_tc2_kernel(const __grid_constant__ CUtensorMap tm_p0A, const __grid_constant__ CUtensorMap tm_p1A,
                     const __grid_constant__ CUtensorMap tm_p0B, const __grid_constant__ CUtensorMap tm_p1B,
@@ -137,6 +138,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* drain = tmem_empty + 2;
   uint64_t* never = drain + 1;  // fault injection: nothing arrives on it
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
+  // the epilogue warps' staging buffers, after the 256 bytes of barriers
+  float* trbuf = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256);
   __shared__ int s_abort;
   __shared__ epi::Shared s_epi;
 
@@ -352,7 +355,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int u = cl; u < nsuper; u += ncl) {
       const int t = 2 * u + (int)rank;
       const int rc = epi::tile<SPLIT, false, RO, true>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag, s_epi,
-                                                        ew, q, lane, empty_cl);
+                                                        ew, q, lane, trbuf + ew * epi::TR_FLOATS, empty_cl);
       if (rc < 0) {
         if (lane == 0) st_cluster_u32(peer_abort, 1u);
         break;
@@ -394,7 +397,7 @@ cudaError_t set_smem_once(K kernel, int bytes, int which) {
 size_t syrk_tc2_smem_bytes(bool split) {
   const int stages = split ? tc2::STAGES_SPLIT : tc2::STAGES_PLAIN;
   const int sb = split ? tc2::STAGE_SPLIT : tc2::STAGE_PLAIN;
-  return (size_t)stages * sb + 1024 /* alignment slack */ + 256 /* barriers */;
+  return (size_t)stages * sb + 1024 /* alignment slack */ + 256 /* barriers */ + epi::TR_BYTES;
 }
 
 cudaError_t launch_syrk_tc2(const SqArgs& a, const CUtensorMap* tm, bool split, int grid, cudaStream_t st) {
