@@ -45,14 +45,31 @@ constexpr int SLOTS = 4;
 // three dots (tr Yin, <Yin, aux>, <P, aux>)
 constexpr int NRED = 5;
 
+// A tile's sums handed from the epilogue warps to the finisher warp, which
+// publishes them and, for the last tile of an instance, runs its control
+// step (off the epilogue warps' path: that work is a chain of global
+// round trips).
+constexpr int FQ = 4;
+struct FinEntry {
+  int t, b, out_mode, dots;
+  double T, Q, d0, d1, d2;
+};
+
 struct Shared {
   double red[SLOTS][WARPS][NRED];
   int cnt[SLOTS];
+  FinEntry fq[FQ];
+  uint64_t fin_full[FQ];   // entry written (one arrive)
+  uint64_t fin_empty[FQ];  // entry read by the finisher (one arrive)
 };
 
-// thread 0, before the kernel's first __syncthreads
+// thread 0, before the kernel's mbarrier-init fence and first __syncthreads
 __device__ __forceinline__ void init(Shared& s) {
   for (int k = 0; k < SLOTS; ++k) s.cnt[k] = 0;
+  for (int k = 0; k < FQ; ++k) {
+    sp2::tc::mbar_init(&s.fin_full[k], 1);
+    sp2::tc::mbar_init(&s.fin_empty[k], 1);
+  }
 }
 
 __device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
@@ -528,29 +545,71 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
     last = (atomicAdd(&sh.cnt[slot], 1) == WARPS - 1) ? 1u : 0u;
   }
   last = __shfl_sync(0xffffffffu, last, 0);
-  if (last) {
+  if (last && lane == 0) {
+    // the last warp of the tile sums the partials in warp order and hands
+    // them to the finisher warp (entry `it` of its queue)
     __threadfence_block();
-    double T = 0.0, Q = 0.0;
-    if (lane == 0) {
-      volatile double* rd = &sh.red[slot][0][0];
-      double d0 = 0.0, d1 = 0.0, d2 = 0.0;
-      for (int k = 0; k < WARPS; ++k) {
-        T += rd[NRED * k];
-        Q += rd[NRED * k + 1];
-        d0 += rd[NRED * k + 2];
-        d1 += rd[NRED * k + 3];
-        d2 += rd[NRED * k + 4];
-      }
-      if (ADJ || energy) {
-        a.tile_dots[3 * (long long)t + 0] = d0;
-        a.tile_dots[3 * (long long)t + 1] = d1;
-        a.tile_dots[3 * (long long)t + 2] = d2;
-      }
-      sh.cnt[slot] = 0;
+    volatile double* rd = &sh.red[slot][0][0];
+    double T = 0.0, Q = 0.0, d0 = 0.0, d1 = 0.0, d2 = 0.0;
+    for (int k = 0; k < WARPS; ++k) {
+      T += rd[NRED * k];
+      Q += rd[NRED * k + 1];
+      d0 += rd[NRED * k + 2];
+      d1 += rd[NRED * k + 3];
+      d2 += rd[NRED * k + 4];
     }
-    finish_tile_warp(a, t, b, T, Q, p.out_mode);
+    sh.cnt[slot] = 0;
+    const uint32_t e = it % FQ;
+    if (mbar_wait(&sh.fin_empty[e], ((it / FQ) & 1u) ^ 1u, abort_flag, lim)) {
+      FinEntry& f = sh.fq[e];
+      f.t = t;
+      f.b = b;
+      f.out_mode = p.out_mode;
+      f.dots = (ADJ || energy) ? 1 : 0;
+      f.T = T;
+      f.Q = Q;
+      f.d0 = d0;
+      f.d1 = d1;
+      f.d2 = d2;
+      mbar_arrive(&sh.fin_full[e]);
+    } else {
+      atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
+    }
   }
   return 1;
+}
+
+// The finisher warp: for every active tile of the CTA, in the order the
+// epilogue warps take them (tile(t) for t = first, first + stride, ...),
+// waits for the tile's entry, writes its per-tile sums and runs
+// finish_tile_warp (the instance's control step after its last tile).
+// Returns early on an abort.
+__device__ __forceinline__ void finisher(const SqArgs& a, int first, int stride, int count, Shared& sh,
+                                         volatile int* abort_flag, int lane) {
+  using namespace sp2::tc;
+  const unsigned long long lim = wait_limit(a);
+  uint32_t it = 0;
+  for (int t = first; t < count; t += stride) {
+    int b, I, J, h;
+    unpack_tile(a.tiles[t], b, I, J, h);
+    if (!load_params(a, b).active) continue;
+    const uint32_t e = it % FQ;
+    if (!__all_sync(0xffffffffu, mbar_wait(&sh.fin_full[e], (it / FQ) & 1u, abort_flag, lim))) {
+      if (lane == 0) atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
+      *abort_flag = 1;
+      return;
+    }
+    const FinEntry f = sh.fq[e];
+    if (lane == 0 && f.dots) {
+      a.tile_dots[3 * (long long)f.t + 0] = f.d0;
+      a.tile_dots[3 * (long long)f.t + 1] = f.d1;
+      a.tile_dots[3 * (long long)f.t + 2] = f.d2;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sh.fin_empty[e]);
+    finish_tile_warp(a, f.t, f.b, f.T, f.Q, f.out_mode);
+    ++it;
+  }
 }
 
 }  // namespace epi

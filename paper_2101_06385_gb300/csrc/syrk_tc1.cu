@@ -12,11 +12,12 @@
 // fills the other with tile t+1, and the epilogue (FP32 update, re-split,
 // row and mirrored stores, traces) runs under the next tile's MMAs.
 //
-// CTA = 10 warps, persistent over the upper-tile list (one CTA per SM):
+// CTA = 11 warps, persistent over the upper-tile list (one CTA per SM):
 //   warp 0      TMA producer (one thread): hp, lo' of the 128 A rows and of
 //               the 256 B rows per 64-wide K stage (96 KB, 2 stages)
 //   warp 1      TMEM allocation + MMA issuer (one thread)
 //   warps 2..9  epilogue: TMEM lane quarter (warp % 4) x column half
+//   warp 10     finisher: publishes each tile's sums, runs the control steps
 // Plain FP16 (split = false): hi hi only, 48 KB stages, 4 stages.
 // Every mbarrier wait is bounded; see syrk_tc.cu for the time-out path.
 #include <cuda.h>
@@ -37,7 +38,8 @@ constexpr int STAGE_PLAIN = A_BYTES + B_BYTES;          // 48 KB: hiA hiB
 constexpr int STAGES_SPLIT = 2;
 constexpr int STAGES_PLAIN = 4;
 constexpr int EPI_WARPS = epi::WARPS;
-constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int FIN_WARP = 2 + EPI_WARPS;  // the finisher warp (after the epilogue warps)
+constexpr int THREADS = 64 + 32 * EPI_WARPS + 32;
 constexpr uint32_t TMEM_COLS = 512;  // two 256-column accumulators
 
 // stage offsets (split): hpA, loA (A_BYTES each), hpB, loB (B_BYTES each)
@@ -217,6 +219,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
     }
+  } else if (warp == FIN_WARP) {
+    // ------------------------------------------------------------ finisher
+    epi::finisher(a, blockIdx.x, gridDim.x, a.ntiles, s_epi, abort_flag, lane);
   } else {
     // ------------------------------------------------------------ epilogue
     const int ew = warp - 2;  // 0..7

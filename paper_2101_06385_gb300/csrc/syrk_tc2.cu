@@ -33,10 +33,11 @@
 // two commutes with every rounding.  Two accumulators fill the 512 TMEM
 // columns: the epilogue of tile t runs under the MMAs of tile t+1.
 //
-// CTA = 10 warps, persistent over the super-tile list (one CTA per SM):
+// CTA = 11 warps, persistent over the super-tile list (one CTA per SM):
 //   warp 0      TMA producer (one thread)
 //   warp 1      TMEM allocation (both CTAs) + MMA issuer (even CTA, one thread)
 //   warps 2..9  epilogue of the CTA's 128 rows (csrc/epilogue.cuh)
+//   warp 10     finisher: publishes each tile's sums, runs the control steps
 // Plain FP16 (split = false): hi hi only, 32 KB stages, 6 stages.
 //
 // Operand reads use only the upper super tiles of the planes: a 64-wide K
@@ -66,7 +67,8 @@ constexpr int STAGE_PLAIN = 2 * HALF_BYTES;  // 32 KB: hiA hiB
 constexpr int STAGES_SPLIT = 3;
 constexpr int STAGES_PLAIN = 6;
 constexpr int EPI_WARPS = epi::WARPS;
-constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int FIN_WARP = 2 + EPI_WARPS;  // the finisher warp (after the epilogue warps)
+constexpr int THREADS = 64 + 32 * EPI_WARPS + 32;
 constexpr uint32_t TMEM_COLS = 512;  // two 256-column accumulators
 
 // Instruction descriptor of the pair MMA: M = 256 (bits 24-28 = M >> 4),
@@ -346,6 +348,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
     }
+  } else if (warp == FIN_WARP) {
+    // ------------------------------------------------------------ finisher
+    // (tiles t = 2 u + rank of u = cl, cl + ncl, ...)
+    epi::finisher(a, 2 * cl + (int)rank, 2 * ncl, 2 * nsuper, s_epi, abort_flag, lane);
+    if (*abort_flag && lane == 0) st_cluster_u32(peer_abort, 1u);
   } else {
     // ------------------------------------------------------------ epilogue
     const int ew = warp - 2;  // 0..7
