@@ -273,9 +273,12 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
     }
     const int ce = c0 + 4 * c4;  // this lane's first column
     // the one diagonal element a lane holds (chunk c0 == R0 of a diagonal
-    // tile): row = column = rdiag, register 4 c4 + r4
-    const bool dlane = !mirror && c0 == R0 && rdiag < N;
+    // tile, a warp-uniform condition): row = column = rdiag, register 4 c4 + r4
+    const bool dchunk = !mirror && c0 == R0;
+    const bool dlane = dchunk && rdiag < N;
     const int id = 4 * c4 + r4;
+    // every row and column of the chunk inside the matrix (warp-uniform)
+    const bool full = nrows == 32 && c0 + 32 <= N;
     // old values first: their global-load latency overlaps the TMEM load
     float y[32];
 #pragma unroll
@@ -306,37 +309,51 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
                                            __uint_as_float(v[4 * m + 2]), __uint_as_float(v[4 * m + 3]));
     }
     __syncwarp();
+    // the diagonal element's old value and product (diagonal chunks only;
+    // P(4 c4 + r4, 4 c4 + r4) sits in this lane's row group c4, component r4)
     float yold_d = 0.f, p_d = 0.f;
+    if (dchunk) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if (k == id) yold_d = y[k];
+      const float4 pdv = *tr_at(trb, 4 * c4 + r4, c4);
+      p_d = (r4 == 0 ? pdv.x : r4 == 1 ? pdv.y : r4 == 2 ? pdv.z : pdv.w) * unscale;
+    }
     {
+      // cb * unscale is exact (a power of two): y' = ca y + (cb 2^-2s) P_acc
+      const float cbu = p.cb * unscale;
       float gy = 0.f, py = 0.f;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const float4 pv = *tr_at(trb, 4 * i + r4, c4);
-        const float P[4] = {pv.x * unscale, pv.y * unscale, pv.z * unscale, pv.w * unscale};
-        const bool rok = 4 * i + r4 < nrows;
-        float x[4] = {0.f, 0.f, 0.f, 0.f};
-        if (ADJ && rok) {
-          const float4 xv = ld4(a.aux + (long long)b * a.slot_y + (long long)(R0 + 4 * i + r4) * ld + ce, ce, N, vec_y);
-          x[0] = xv.x;
-          x[1] = xv.y;
-          x[2] = xv.z;
-          x[3] = xv.w;
+        const float P[4] = {pv.x, pv.y, pv.z, pv.w};
+        if (ADJ) {
+          // dots on the old values (before the update overwrites y)
+          float x[4] = {0.f, 0.f, 0.f, 0.f};
+          if (4 * i + r4 < nrows) {
+            const float4 xv =
+                ld4(a.aux + (long long)b * a.slot_y + (long long)(R0 + 4 * i + r4) * ld + ce, ce, N, vec_y);
+            x[0] = xv.x;
+            x[1] = xv.y;
+            x[2] = xv.z;
+            x[3] = xv.w;
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            gy = fmaf(y[4 * i + e], x[e], gy);
+            py = fmaf(P[e] * unscale, x[e], py);
+          }
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int k = 4 * i + e;
-          if (ADJ) {
-            // dots on the old values (before the update overwrites y)
-            gy = fmaf(y[k], x[e], gy);
-            py = fmaf(P[e], x[e], py);
-          }
-          if (dlane && k == id) {
-            yold_d = y[k];
-            p_d = P[e];
-          }
-          const float yn = fmaf(p.ca, y[k], p.cb * P[e]);
-          y[k] = (rok && ce + e < N) ? yn : 0.f;
-        }
+        for (int e = 0; e < 4; ++e) y[4 * i + e] = fmaf(p.ca, y[4 * i + e], cbu * P[e]);
+      }
+      if (!full) {
+        // rows past nrows and columns past N stay zero
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (!(4 * i + r4 < nrows && ce + e < N)) y[4 * i + e] = 0.f;
       }
       if (ADJ) {
         dgy += (double)gy;
@@ -348,15 +365,17 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
     // one FP64 update per diagonal element, outside the unrolled element loop
     float ydo = 0.f;
     double yd = 0.0;
-    if (dlane) {
-      const double pd = (a.rn || a.rnp_in) ? rn_l : (double)p_d;
-      yd = p.ca_d * (double)yold_d + p.cb_d * pd + p.cc_d;
-      tr += yd;
+    if (dchunk) {
+      if (dlane) {
+        const double pd = (a.rn || a.rnp_in) ? rn_l : (double)p_d;
+        yd = p.ca_d * (double)yold_d + p.cb_d * pd + p.cc_d;
+        tr += yd;
+        ydo = outD ? (float)(yd + p.alpha_out) : (float)yd;
+      }
       const float ydf = (float)yd;
-      ydo = outD ? (float)(yd + p.alpha_out) : ydf;
 #pragma unroll
       for (int k = 0; k < 32; ++k)
-        if (k == id) y[k] = ydf;
+        if (dlane && k == id) y[k] = ydf;
     }
     // sums of squares of Y': per row (over the chunk's 32 columns) and per
     // column (over the warp's 32 rows), and this lane's share of ||Y'||_F^2
@@ -366,9 +385,8 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       rs[i] = 0.f;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float s2 = y[4 * i + e] * y[4 * i + e];
-        rs[i] += s2;
-        cs[e] += s2;
+        rs[i] = fmaf(y[4 * i + e], y[4 * i + e], rs[i]);
+        cs[e] = fmaf(y[4 * i + e], y[4 * i + e], cs[e]);
       }
     }
     sq += (double)(((rs[0] + rs[1]) + (rs[2] + rs[3])) + ((rs[4] + rs[5]) + (rs[6] + rs[7])));
@@ -426,14 +444,17 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
       if (outD) ydo = (float)(1.0 - rd);
     }
     if (outD) {
+      // D's diagonal: alpha + Y'_ii in FP64, rounded once
+      if (dchunk) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          if (dlane && k == id) y[k] = ydo;
+      }
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        if (4 * i + r4 < nrows) {
-          float d_[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) d_[e] = (dlane && 4 * i + e == id) ? ydo : y[4 * i + e];
-          st4(D + (long long)(R0 + 4 * i + r4) * N + ce, make_float4(d_[0], d_[1], d_[2], d_[3]), ce, N, vec_n);
-        }
+        if (4 * i + r4 < nrows)
+          st4(D + (long long)(R0 + 4 * i + r4) * N + ce, make_float4(y[4 * i], y[4 * i + 1], y[4 * i + 2], y[4 * i + 3]),
+              ce, N, vec_n);
       }
       if (!ADJ && a.Hobs) {
         // Tr[D A] over this chunk (A symmetric: the mirror counts twice below)
@@ -444,7 +465,7 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
             const float4 hv = ld4(a.Hobs[b] + (long long)(R0 + 4 * i + r4) * N + ce, ce, N, vec_n);
             const float hx[4] = {hv.x, hv.y, hv.z, hv.w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) eo = fmaf((dlane && 4 * i + e == id) ? ydo : y[4 * i + e], hx[e], eo);
+            for (int e = 0; e < 4; ++e) eo = fmaf(y[4 * i + e], hx[e], eo);
           }
         }
         dtr += (double)eo;
@@ -462,16 +483,19 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         if (4 * i + r4 < nrows) {
+          // Eq. 12 on pairs of elements: hi = fp16(x), lo' = fp16(2^s (x - hi));
+          // hp = 2^s hi is exact in FP16 (|x| < 16), so one packed multiply
           uint32_t pa[2], pl[2];
+          const __half2 s2 = __float2half2_rn(lo_scale);
 #pragma unroll
           for (int e2 = 0; e2 < 2; ++e2) {
-            __half h0, l0, h1, l1;
-            split_fp16(y[4 * i + 2 * e2], lo_scale, h0, l0);
-            split_fp16(y[4 * i + 2 * e2 + 1], lo_scale, h1, l1);
-            pa[e2] = SPLIT ? pack_h2(__float2half_rn(__half2float(h0) * lo_scale),
-                                     __float2half_rn(__half2float(h1) * lo_scale))
-                           : pack_h2(h0, h1);
-            pl[e2] = pack_h2(l0, l1);
+            const float x0 = y[4 * i + 2 * e2], x1 = y[4 * i + 2 * e2 + 1];
+            const __half2 h2 = __floats2half2_rn(x0, x1);
+            const float2 hf = __half22float2(h2);
+            const __half2 l2 = __floats2half2_rn((x0 - hf.x) * lo_scale, (x1 - hf.y) * lo_scale);
+            const __half2 p2 = SPLIT ? __hmul2(h2, s2) : h2;
+            pa[e2] = *reinterpret_cast<const uint32_t*>(&p2);
+            pl[e2] = *reinterpret_cast<const uint32_t*>(&l2);
           }
           const long long off = (long long)(R0 + 4 * i + r4) * ldh + ce;
           if (pa_out) *reinterpret_cast<uint2*>(pa_out + off) = make_uint2(pa[0], pa[1]);
