@@ -357,12 +357,13 @@ def _bench_batched(sp2, sp2_inputs, dev, reps=3, count=512):
                          "trace_err_worst": max(tr_errs), "reference": "closed form Q_occ Q_occ^T, whole D"}}
 
 
-def _bench_network(sp2, sp2_inputs, dev, B=64, N=2048, L=20, ckpt_every=5, reps=2, grad_check=True):
+def _bench_network(sp2, sp2_inputs, dev, B=64, N=2048, L=20, ckpt_every=5, reps=2, grad_check=True, gen="gpu"):
     """Differentiable network: 64 gapped Hamiltonians of N = 2048, 20 layers,
     coefficients initialised to the SP2 branch values of instance 0."""
     import torch
 
-    hs = [sp2_inputs.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), 2000 + i, device=str(dev))
+    hs = [sp2_inputs.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), 2000 + i,
+                                        device=str(dev) if gen == "gpu" else "cpu")
           for i in range(B)]
     H = torch.from_numpy(np.stack([x.h32() for x in hs])).to(dev)
     _, st = sp2.density_matrix(H[0].contiguous(), N // 2, precision="split")
@@ -453,14 +454,15 @@ def _network_grad_check(sp2, sp2_inputs, dev, H, hs, coef, ckpt_every, sub=2, h=
             "loss": "(1/B) sum ||X_L - D_FD||_F^2, D_FD at kT = 0.05, mu = 0"}
 
 
-def _bench_fermi(sp2, sp2_inputs, dev, B=64, N=2048, L=11, reps=3):
+def _bench_fermi(sp2, sp2_inputs, dev, B=64, N=2048, L=11, reps=3, gen="gpu"):
     """Finite-temperature expansion (11 generalised layers with the readout
     fused into the squaring epilogue) on the network workload's 64 instances
     of N = 2048.  The timing does not depend on the coefficient values; the
     SP2 branch polynomials with the readout on the last layer are used."""
     import torch
 
-    Hs = [sp2_inputs.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), 2000 + i, device=str(dev)).h32()
+    Hs = [sp2_inputs.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), 2000 + i,
+                                        device=str(dev) if gen == "gpu" else "cpu").h32()
           for i in range(B)]
     H = torch.from_numpy(np.stack(Hs)).to(dev)
     theta = np.array([[1.0, 0.0, 0.0] if n % 2 else [-1.0, 2.0, 0.0] for n in range(L)])
@@ -702,9 +704,9 @@ def run_only(args):
     if args.only == "batched":
         out = _bench_batched(sp2, sp2_inputs, dev, reps=max(1, args.steps), count=args.batched_count)
     elif args.only == "fermi":
-        out = _bench_fermi(sp2, sp2_inputs, dev, reps=max(1, args.steps))
+        out = _bench_fermi(sp2, sp2_inputs, dev, reps=max(1, args.steps), gen=args.gen_device)
     else:
-        out = _bench_network(sp2, sp2_inputs, dev, reps=max(1, args.steps))
+        out = _bench_network(sp2, sp2_inputs, dev, reps=max(1, args.steps), gen=args.gen_device)
     print(json.dumps({"only": args.only, **out}))
     return 0
 
