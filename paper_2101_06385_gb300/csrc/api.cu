@@ -1573,8 +1573,13 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
       plan.params[(size_t)n * B + b].out_mode = OUT_Y;
       plan.params[(size_t)n * B + b].alpha_out = 0.0;
     }
+  // CTA pairs (M = 256 MMAs) unless the single-CTA kernel was selected; the
+  // pair kernel keeps the operand planes as upper super tiles
+  const bool pairs = g.pair_kernel;
+  const int nmap = pairs ? 6 : 4;
+  const int boxb = pairs ? kTcBM : kTcBN;
   int ntiles = 0;
-  CKS(upload_tiles(N, B, 1, &ntiles));
+  CKS(upload_tiles(N, B, pairs ? 2 : 1, &ntiles));
   const long long ld_h = round_up(N, 64), slot_h = ld_h * N;
   void *params, *params2, *nal, *rn, *err, *seg, *segp, *gh[2], *gl[2] = {nullptr, nullptr}, *dots, *tdots;
   CKS(ws(B_PARAMS, plan.params.size() * sizeof(LayerParams), &params));
@@ -1614,11 +1619,11 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
   // (hp or hi) and gl (lo')
   auto segp0 = [&](int k) { return (__half*)((char*)segp + plane_bytes * nplanes * k); };
   auto segp1 = [&](int k) { return split ? (__half*)((char*)segp + plane_bytes * (nplanes * k + 1)) : nullptr; };
-  std::vector<CUtensorMap> mY((size_t)ce * 4);
-  for (int k = 0; k < ce; ++k) CKS(tmaps4_for(segp0(k), segp1(k), N, B, ld_h, slot_h, &mY[(size_t)k * 4]));
-  CUtensorMap mG4[2][4];
-  CKS(tmaps4_for(gh[0], gl[0], N, B, ld_h, slot_h, mG4[0]));
-  CKS(tmaps4_for(gh[1], gl[1], N, B, ld_h, slot_h, mG4[1]));
+  std::vector<CUtensorMap> mY((size_t)ce * 6);
+  for (int k = 0; k < ce; ++k) CKS(tmaps4_for(segp0(k), segp1(k), N, B, ld_h, slot_h, &mY[(size_t)k * 6], boxb));
+  CUtensorMap mG4[2][6];
+  CKS(tmaps4_for(gh[0], gl[0], N, B, ld_h, slot_h, mG4[0], boxb));
+  CKS(tmaps4_for(gh[1], gl[1], N, B, ld_h, slot_h, mG4[1], boxb));
   const float ls = std::ldexp(1.0f, g.lo_scale_exp);
   SqArgs A;
   memset(&A, 0, sizeof(A));
@@ -1642,7 +1647,7 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
   const int sgrid = (int)std::min<long long>((long long)N * B, 8LL * g.num_sms);
   const int mgrid = (int)std::min<long long>(N, std::max(1, 4 * g.num_sms / B + 1));
   const int rgrid = (int)std::min<long long>((N + 7) / 8, std::max(1, 2 * g.num_sms / B + 1));
-  const int tgrid = std::min(ntiles, g.num_sms);
+  const int tgrid = std::min(ntiles, g.num_sms) & (pairs ? ~1 : ~0);
   auto segY = [&](int i) { return (float*)seg + (size_t)i * B * slot; };
   void* rnp[2];
   SqArgs R0 = A;  // row-norm carry of the recomputation (rnp_for sets its strides)
@@ -1677,14 +1682,30 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
       rnp_step(F, rnp, k);
       F.lp = (const LayerParams*)params + (size_t)n * B;
       F.nseg = 1;
-      CK(launch_syrk_tc1(F, &mY[(size_t)k * 4], split, tgrid, st));
+      F.tri_planes = pairs ? 1 : 0;
+      if (pairs)
+        CK(launch_syrk_tc2(F, &mY[(size_t)k * 6], split, tgrid, st));
+      else
+        CK(launch_syrk_tc1(F, &mY[(size_t)k * 6], split, tgrid, st));
     }
     for (int n = n1 - 1; n >= n0; --n) {
       const int k = n - n0;
       float* Yn = segY(k);
-      const CUtensorMap* mYk = &mY[(size_t)k * 4];
-      // segment 1: Y_n rows x G rows (Y G), segment 2: G rows x Y_n rows (G Y)
-      CUtensorMap m8[8] = {mYk[0], mYk[1], mG4[cur][2], mG4[cur][3], mG4[cur][0], mG4[cur][1], mYk[2], mYk[3]};
+      const CUtensorMap* mYk = &mY[(size_t)k * 6];
+      const CUtensorMap* mGk = mG4[cur];
+      // segment 1: Y_n rows x G rows (Y G), segment 2: G rows x Y_n rows (G Y);
+      // the pair kernel takes per segment {A, A lo, B, B lo, A transposed,
+      // A lo transposed} and reads B's transposed blocks through the other
+      // segment's A maps
+      CUtensorMap m8[12];
+      if (pairs) {
+        const CUtensorMap t[12] = {mYk[0], mYk[1], mGk[2], mGk[3], mYk[4], mYk[5],
+                                   mGk[0], mGk[1], mYk[2], mYk[3], mGk[4], mGk[5]};
+        for (int i = 0; i < 12; ++i) m8[i] = t[i];
+      } else {
+        const CUtensorMap t[8] = {mYk[0], mYk[1], mGk[2], mGk[3], mGk[0], mGk[1], mYk[2], mYk[3]};
+        for (int i = 0; i < 8; ++i) m8[i] = t[i];
+      }
       SqArgs Bk = A;
       Bk.Yin = (float*)G;
       Bk.Yout = (float*)G;
@@ -1697,7 +1718,11 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
       Bk.aux = Yn;
       Bk.tile_dots = (double*)tdots;
       Bk.dots_out = (double*)dots + (size_t)n * B * 3;
-      CK(launch_syrk_tc1(Bk, m8, split, tgrid, st));
+      Bk.tri_planes = pairs ? 1 : 0;
+      if (pairs)
+        CK(launch_syrk_tc2(Bk, m8, split, tgrid, st));
+      else
+        CK(launch_syrk_tc1(Bk, m8, split, tgrid, st));
       cur ^= 1;
     }
   }

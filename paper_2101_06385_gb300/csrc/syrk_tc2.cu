@@ -119,15 +119,21 @@ __device__ __forceinline__ bool epoch_wait(const unsigned* ctr, unsigned need, u
 }
 
 // RO: readout mode of the epilogue (finite-temperature expansion).
+// NSEG2: P = A_1 B_1^T + A_2 B_2^T over two K segments (the tm2 maps hold the
+// second segment's operands) with the adjoint-mode epilogue: the split SYR2K
+// Y G + G Y of the network adjoint (both factors symmetric).
 // tm_p0A/p1A: planes with 64 x 128 boxes (the A half); tm_p0B/p1B: the same
 // boxes for the B half; tm_p0T / tm_p1T: 64 x 64 boxes (transposed reads).
-template <bool SPLIT, bool RO>
-
-__global__ void __launch_bounds__(THREADS, 1)
-    syrk_tc2_kernel(const __grid_constant__ CUtensorMap tm_p0A, const __grid_constant__ CUtensorMap tm_p1A,
-                    const __grid_constant__ CUtensorMap tm_p0B, const __grid_constant__ CUtensorMap tm_p1B,
-                    const __grid_constant__ CUtensorMap tm_p0T, const __grid_constant__ CUtensorMap tm_p1T,
-                    const SqArgs a) {
+// The kernel body; the map arguments point at the kernels' __grid_constant__
+// parameters (for one segment the second set repeats the first).
+template <bool SPLIT, bool RO, bool NSEG2>
+__device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const CUtensorMap& tm_p1A,
+                                              const CUtensorMap& tm_p0B, const CUtensorMap& tm_p1B,
+                                              const CUtensorMap& tm_p0T, const CUtensorMap& tm_p1T,
+                                              const CUtensorMap& tm2_p0A, const CUtensorMap& tm2_p1A,
+                                              const CUtensorMap& tm2_p0B, const CUtensorMap& tm2_p1B,
+                                              const CUtensorMap& tm2_p0T, const CUtensorMap& tm2_p1T,
+                                              const SqArgs& a) {
   constexpr int STAGES = SPLIT ? STAGES_SPLIT : STAGES_PLAIN;
   constexpr int STAGE_BYTES = SPLIT ? STAGE_SPLIT : STAGE_PLAIN;
 
@@ -205,14 +211,17 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int N = a.Ns[b];
         const int rowA = I * BN + (int)rank * BH, rowB = J * BN + (int)rank * BH;
         const int nk = (N + BK - 1) / BK;
+        const int nkt = NSEG2 ? 2 * nk : nk;  // K stages of the tile over both segments
         const bool rev = a.snake && (((u - cl) / ncl) & 1);
-        for (int kk = 0; kk < nk; ++kk, ++gs) {
-          const int kb = rev ? nk - 1 - kk : kk;
+        for (int kk = 0; kk < nkt; ++kk, ++gs) {
+          const int kbt = rev ? nkt - 1 - kk : kk;
+          const bool seg2 = NSEG2 && kbt >= nk;
+          const int kb = seg2 ? kbt - nk : kbt;  // K block within its segment
           if (pub_sync && gs > 0 && gs % (uint32_t)W == 0) {
             const uint32_t e = gs / (uint32_t)W - 1u;  // the epoch this pair just finished
             atomicAdd(&a.wave_ctr[e], 1u);
             if (wait_sync && e >= 1u)
-              wait_sync = epoch_wait(a.wave_ctr + (e - 1u), pairs_in_epoch(e - 1u, W, nk, nsuper, ncl), lim);
+              wait_sync = epoch_wait(a.wave_ctr + (e - 1u), pairs_in_epoch(e - 1u, W, nkt, nsuper, ncl), lim);
           }
           if (!mbar_wait_cl(&empty[stage], phase ^ 1u, abort_flag, lim)) {
             ok = false;
@@ -226,14 +235,24 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t bar = full_cl + 8u * (uint32_t)stage;
           const int k0 = kb * BK;
           const int ks = k0 / BN;  // super column of this K block
+          // the second segment's A and B come from the other matrix of the
+          // product (their transposed reads too)
+          const CUtensorMap* mA0 = seg2 ? &tm2_p0A : &tm_p0A;
+          const CUtensorMap* mA1 = seg2 ? &tm2_p1A : &tm_p1A;
+          const CUtensorMap* mB0 = seg2 ? &tm2_p0B : &tm_p0B;
+          const CUtensorMap* mB1 = seg2 ? &tm2_p1B : &tm_p1B;
+          const CUtensorMap* mAT0 = seg2 ? &tm2_p0T : &tm_p0T;
+          const CUtensorMap* mAT1 = seg2 ? &tm2_p1T : &tm_p1T;
+          const CUtensorMap* mBT0 = NSEG2 ? (seg2 ? &tm_p0T : &tm2_p0T) : &tm_p0T;
+          const CUtensorMap* mBT1 = NSEG2 ? (seg2 ? &tm_p1T : &tm2_p1T) : &tm_p1T;
           if (SPLIT) {
-            load_half(st + OFF_HPA, &tm_p0A, &tm_p0T, ks < I, rowA, k0, b, bar);
-            load_half(st + OFF_LOA, &tm_p1A, &tm_p1T, ks < I, rowA, k0, b, bar);
-            load_half(st + OFF_HPB, &tm_p0B, &tm_p0T, ks < J, rowB, k0, b, bar);
-            load_half(st + OFF_LOB, &tm_p1B, &tm_p1T, ks < J, rowB, k0, b, bar);
+            load_half(st + OFF_HPA, mA0, mAT0, ks < I, rowA, k0, b, bar);
+            load_half(st + OFF_LOA, mA1, mAT1, ks < I, rowA, k0, b, bar);
+            load_half(st + OFF_HPB, mB0, mBT0, ks < J, rowB, k0, b, bar);
+            load_half(st + OFF_LOB, mB1, mBT1, ks < J, rowB, k0, b, bar);
           } else {
-            load_half(st, &tm_p0A, &tm_p0T, ks < I, rowA, k0, b, bar);
-            load_half(st + HALF_BYTES, &tm_p0B, &tm_p0T, ks < J, rowB, k0, b, bar);
+            load_half(st, mA0, mAT0, ks < I, rowA, k0, b, bar);
+            load_half(st + HALF_BYTES, mB0, mBT0, ks < J, rowB, k0, b, bar);
           }
           if (++stage == STAGES) {
             stage = 0;
@@ -281,6 +300,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!load_params(a, b).active) continue;
         const int N = a.Ns[b];
         const int nk = (N + BK - 1) / BK;
+        const int nkt = NSEG2 ? 2 * nk : nk;
         const bool rev = a.snake && (((u - cl) / ncl) & 1);
         const uint32_t buf = it & 1u;
         (void)h;
@@ -291,8 +311,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         tc_fence_after();
         const uint32_t d = tmem_base + buf * BN;
-        for (int kk = 0; kk < nk; ++kk) {
-          const int kb = rev ? nk - 1 - kk : kk;
+        for (int kk = 0; kk < nkt; ++kk) {
+          const int kbt = rev ? nkt - 1 - kk : kk;
+          const int kb = (NSEG2 && kbt >= nk) ? kbt - nk : kbt;  // K block within its segment
           if (!mbar_wait_cl(&full[stage], phase, abort_flag, lim)) {
             ok = false;
             break;
@@ -361,7 +382,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t it = 0;
     for (int u = cl; u < nsuper; u += ncl) {
       const int t = 2 * u + (int)rank;
-      const int rc = epi::tile<SPLIT, false, RO, true>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag, s_epi,
+      const int rc = epi::tile<SPLIT, NSEG2, RO, true>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag, s_epi,
                                                         ew, q, lane, trbuf + ew * epi::TR_FLOATS, empty_cl);
       if (rc < 0) {
         if (lane == 0) st_cluster_u32(peer_abort, 1u);
@@ -383,6 +404,30 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+template <bool SPLIT, bool RO>
+__global__ void __launch_bounds__(THREADS, 1)
+    syrk_tc2_kernel(const __grid_constant__ CUtensorMap tm_p0A, const __grid_constant__ CUtensorMap tm_p1A,
+                    const __grid_constant__ CUtensorMap tm_p0B, const __grid_constant__ CUtensorMap tm_p1B,
+                    const __grid_constant__ CUtensorMap tm_p0T, const __grid_constant__ CUtensorMap tm_p1T,
+                    const SqArgs a) {
+  syrk_tc2_body<SPLIT, RO, false>(tm_p0A, tm_p1A, tm_p0B, tm_p1B, tm_p0T, tm_p1T, tm_p0A, tm_p1A, tm_p0B, tm_p1B,
+                                  tm_p0T, tm_p1T, a);
+}
+
+// Two K segments (the network adjoint's Y G + G Y): six maps per segment.
+template <bool SPLIT>
+__global__ void __launch_bounds__(THREADS, 1)
+    syrk_tc2_seg2_kernel(const __grid_constant__ CUtensorMap tm_p0A, const __grid_constant__ CUtensorMap tm_p1A,
+                         const __grid_constant__ CUtensorMap tm_p0B, const __grid_constant__ CUtensorMap tm_p1B,
+                         const __grid_constant__ CUtensorMap tm_p0T, const __grid_constant__ CUtensorMap tm_p1T,
+                         const __grid_constant__ CUtensorMap tm2_p0A, const __grid_constant__ CUtensorMap tm2_p1A,
+                         const __grid_constant__ CUtensorMap tm2_p0B, const __grid_constant__ CUtensorMap tm2_p1B,
+                         const __grid_constant__ CUtensorMap tm2_p0T, const __grid_constant__ CUtensorMap tm2_p1T,
+                         const SqArgs a) {
+  syrk_tc2_body<SPLIT, false, true>(tm_p0A, tm_p1A, tm_p0B, tm_p1B, tm_p0T, tm_p1T, tm2_p0A, tm2_p1A, tm2_p0B,
+                                    tm2_p1B, tm2_p0T, tm2_p1T, a);
+}
+
 }  // namespace tc2
 
 // The dynamic shared-memory opt-in, once per kernel and device (not a stream
@@ -390,7 +435,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 namespace {
 template <typename K>
 cudaError_t set_smem_once(K kernel, int bytes, int which) {
-  static int done_dev[4] = {-1, -1, -1, -1};
+  static int done_dev[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -422,26 +467,24 @@ cudaError_t launch_syrk_tc2(const SqArgs& a, const CUtensorMap* tm, bool split, 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  auto go = [&](auto kernel, int which) -> cudaError_t {
+    cudaError_t e = set_smem_once(kernel, (int)smem, which);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, kernel, tm[0], tm[1], tm[2], tm[3], tm[4], tm[5], a);
+  };
+  auto go2 = [&](auto kernel, int which) -> cudaError_t {
+    cudaError_t e = set_smem_once(kernel, (int)smem, which);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, kernel, tm[0], tm[1], tm[2], tm[3], tm[4], tm[5], tm[6], tm[7], tm[8], tm[9],
+                              tm[10], tm[11], a);
+  };
   cudaError_t e;
-  if (a.R) {
-    if (split) {
-      e = set_smem_once(tc2::syrk_tc2_kernel<true, true>, (int)smem, 3);
-      if (e != cudaSuccess) return e;
-      e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<true, true>, tm[0], tm[1], tm[2], tm[3], tm[4], tm[5], a);
-    } else {
-      e = set_smem_once(tc2::syrk_tc2_kernel<false, true>, (int)smem, 2);
-      if (e != cudaSuccess) return e;
-      e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<false, true>, tm[0], tm[1], tm[2], tm[3], tm[4], tm[5], a);
-    }
-  } else if (split) {
-    e = set_smem_once(tc2::syrk_tc2_kernel<true, false>, (int)smem, 1);
-    if (e != cudaSuccess) return e;
-    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<true, false>, tm[0], tm[1], tm[2], tm[3], tm[4], tm[5], a);
-  } else {
-    e = set_smem_once(tc2::syrk_tc2_kernel<false, false>, (int)smem, 0);
-    if (e != cudaSuccess) return e;
-    e = cudaLaunchKernelEx(&cfg, tc2::syrk_tc2_kernel<false, false>, tm[0], tm[1], tm[2], tm[3], tm[4], tm[5], a);
-  }
+  if (a.nseg == 2)
+    e = split ? go2(tc2::syrk_tc2_seg2_kernel<true>, 5) : go2(tc2::syrk_tc2_seg2_kernel<false>, 4);
+  else if (a.R)
+    e = split ? go(tc2::syrk_tc2_kernel<true, true>, 3) : go(tc2::syrk_tc2_kernel<false, true>, 2);
+  else
+    e = split ? go(tc2::syrk_tc2_kernel<true, false>, 1) : go(tc2::syrk_tc2_kernel<false, false>, 0);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
