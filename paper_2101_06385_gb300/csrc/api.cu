@@ -1501,6 +1501,13 @@ sp2_status sp2_network_forward(const float* H, int B, int N, int L, const float*
     if (tc) {
       A.Yin = X_out;
       A.Yout = X_out;
+      // Only the upper super tiles of Y' are stored unless whole rows are read
+      // after this launch (a checkpoint; the last layer writes X_L whole
+      // anyway); the CTA-pair kernel reads its operands from the upper super
+      // tiles of the planes alone, so their mirror is never stored.
+      const bool to_ckpt = ckpt && (n + 1) % ckpt_every == 0;
+      A.tri_y = to_ckpt ? 0 : 1;
+      A.tri_planes = pairs ? 1 : 0;
       A.hi_out = (__half*)hi[cur ^ 1];
       A.lo_out = (__half*)lo[cur ^ 1];
       A.hp_out = (__half*)hp[cur ^ 1];
@@ -1682,6 +1689,9 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
       rnp_step(F, rnp, k);
       F.lp = (const LayerParams*)params + (size_t)n * B;
       F.nseg = 1;
+      // the recomputed iterates are read only on upper super tiles (the next
+      // layer's old values, the adjoint epilogue's aux)
+      F.tri_y = 1;
       F.tri_planes = pairs ? 1 : 0;
       if (pairs)
         CK(launch_syrk_tc2(F, &mY[(size_t)k * 6], split, tgrid, st));
@@ -1718,6 +1728,9 @@ sp2_status sp2_network_backward(const float* H, int B, int N, int L, const float
       Bk.aux = Yn;
       Bk.tile_dots = (double*)tdots;
       Bk.dots_out = (double*)dots + (size_t)n * B * 3;
+      // G is read on upper super tiles only, except after the last adjoint
+      // layer (dL/dX_0 is returned whole)
+      Bk.tri_y = n == 0 ? 0 : 1;
       Bk.tri_planes = pairs ? 1 : 0;
       if (pairs)
         CK(launch_syrk_tc2(Bk, m8, split, tgrid, st));
