@@ -75,6 +75,15 @@ constexpr uint32_t TMEM_COLS = 512;  // two 256-column accumulators
 // N = 256 (bits 17-22 = N >> 3), D = F32, A = B = F16, K-major unless the
 // MN bits are added.
 constexpr uint32_t IDESC2 = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24);
+// N = 128 for super tiles whose columns from J * 256 + 128 on all lie past
+// the matrix (the last super column of an instance with N mod 256 in
+// (0, 128]): each CTA supplies 64 B rows, the accumulator's columns 128-255
+// are not written and the epilogue, which skips columns past the padded K
+// extent, never reads them.
+constexpr uint32_t IDESC2_N128 = (1u << 4) | ((uint32_t)(BH >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24);
+
+// MMA N of super tile column J of an instance of size N
+__device__ __forceinline__ int pair_n(int N, int J) { return N - J * BN <= BH ? BH : BN; }
 
 // one 64 x 64 FP16 box of a transposed read
 constexpr int T_BOX = 64 * 64 * 2;
@@ -149,12 +158,36 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
   // the epilogue warps' staging buffers, after the 256 bytes of barriers
   float* trbuf = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256);
   __shared__ int s_abort;
+  __shared__ int s_work;
   __shared__ epi::Shared s_epi;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
   const uint32_t peer = rank ^ 1u;
+
+  // A pair whose super tiles all belong to finished instances (the launches
+  // after a solve's last layer) leaves before any set-up; one warp looks at
+  // 32 of its tiles at a time.  Both CTAs of the pair reach the same answer:
+  // an instance can finish within this launch only after all of its tiles,
+  // these among them, have been processed.
+  if (warp == 0) {
+    const int c0 = (int)(blockIdx.x >> 1), nc = (int)(gridDim.x >> 1), ns = a.ntiles >> 1;
+    bool any = false;
+    for (int u0 = c0; u0 < ns && !any; u0 += 32 * nc) {
+      const int u = u0 + lane * nc;
+      bool act = false;
+      if (u < ns) {
+        int b, I, J, h;
+        unpack_tile(a.tiles[2 * u], b, I, J, h);
+        act = load_params(a, b).active != 0;
+      }
+      any = __any_sync(0xffffffffu, act);
+    }
+    if (lane == 0) s_work = any ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_work) return;
 
   if (threadIdx.x == 0) {
     s_abort = 0;
@@ -209,7 +242,8 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
         unpack_tile(a.tiles[2 * u + (int)rank], b, I, J, h);
         if (!load_params(a, b).active) continue;
         const int N = a.Ns[b];
-        const int rowA = I * BN + (int)rank * BH, rowB = J * BN + (int)rank * BH;
+        // each CTA supplies half of the MMA's N rows of B
+        const int rowA = I * BN + (int)rank * BH, rowB = J * BN + (int)rank * (pair_n(N, J) >> 1);
         const int nk = (N + BK - 1) / BK;
         const int nkt = NSEG2 ? 2 * nk : nk;  // K stages of the tile over both segments
         const bool rev = a.snake && (((u - cl) / ncl) & 1);
@@ -303,6 +337,7 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
         const int nkt = NSEG2 ? 2 * nk : nk;
         const bool rev = a.snake && (((u - cl) / ncl) & 1);
         const uint32_t buf = it & 1u;
+        const uint32_t idesc_n = pair_n(N, J) == BH ? IDESC2_N128 : IDESC2;
         (void)h;
         // the k-th use of a buffer waits for the epilogues' (k-1)-th release
         if (!mbar_wait_cl(&tmem_empty[buf], ((it >> 1) & 1u) ^ 1u, abort_flag, lim)) {
@@ -323,7 +358,7 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
           // operands left of the diagonal arrived transposed (MN-major)
           const int sc = kb * BK / BN;
           const bool ta = sc < I, tb = sc < J;
-          const uint32_t idesc = IDESC2 | (ta ? IDESC_A_MN : 0u) | (tb ? IDESC_B_MN : 0u);
+          const uint32_t idesc = idesc_n | (ta ? IDESC_A_MN : 0u) | (tb ? IDESC_B_MN : 0u);
 #pragma unroll
           for (int ks = 0; ks < BK / UMMA_K; ++ks) {
             // K step ks: 32 B along a K-major row, or two 8-row K groups
