@@ -310,9 +310,10 @@ sp2_status sp2_observable(const float* D, const float* A, int N, double* out);
 
 /*
  * sp2_density_matrix for callers that cannot allocate device memory when they
- * need D: code that runs while a stream is being captured into a CUDA graph,
- * engines that pre-size every buffer and must not grow the process footprint
- * mid-run, hosts that hand the library only memory they manage themselves.
+ * need D: engines that pre-size every buffer at start-up and must not grow the
+ * process footprint mid-run, real-time loops in which an allocation (which can
+ * synchronise the device) would stall a step, and hosts that hand the library
+ * only memory they manage themselves.
  * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch is
  * one file-scope device array of SP2_NOALLOC_SCRATCH_BYTES (about 8 MiB),
  * which every GPU that loads the library holds until the process exits.

@@ -2,11 +2,11 @@
 // cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc (or any routine that allocates) at the
-// time they need a density matrix: code that runs while a CUDA stream is being
-// captured into a graph (allocation is not a capturable operation), callers
-// that own a fixed memory budget and must not grow the process footprint
-// mid-run (real-time loops, MD engines that pre-size every buffer), and hosts
-// that hand the library only pointers they manage themselves.  This entry
+// time they need a density matrix: callers that own a fixed memory budget and
+// must not grow the process footprint mid-run (MD engines that pre-size every
+// buffer at start-up), real-time loops in which an allocation, which can
+// synchronise the device, would stall a step, and hosts that hand the library
+// only pointers they manage themselves.  This entry
 // point therefore takes all of its scratch from one file-scope device array
 // of fixed size, which the module loader places in device memory when the
 // library is loaded on a GPU; every GPU that loads the library keeps it until

@@ -1,6 +1,8 @@
 """The allocation-free entry point (for callers that cannot allocate device
-memory, e.g. inside stream capture or under a fixed memory budget) gives the
-same density matrix as sp2_density_matrix, call after call, through the C ABI."""
+memory when they need D: a fixed memory budget, a real-time loop that an
+allocation would stall, a host that manages all device memory itself) gives
+the same density matrix as sp2_density_matrix, call after call, through the
+C ABI."""
 import ctypes
 
 import numpy as np
