@@ -113,6 +113,8 @@ struct State {
   // with the synchronisation: K walked backwards on alternate waves
   // (SP2_SNAKE=1; off by default)
   int snake = 0;
+  // wide units for the single solve (SP2_WIDE: 0 off, 1 on, unset: by wave count)
+  int wide = -1;
   unsigned long long wait_ns = 0;  // bound of the squaring kernels' waits (0: 4 s)
 };
 
@@ -172,7 +174,10 @@ inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m
 // that the CTAs running at the same time share row panels in L2.
 // halves: 0 = one tile per block (FFMA kernel), 1 = both 128-row halves of a
 // 256 x 256 super tile unless the second lies past N, 2 = both halves always
-// (adjacent; the CTA-pair kernel takes them together).
+// (adjacent; the CTA-pair kernel takes them together), 3 = as 2, grouped in
+// units of the two super tiles (I, J), (I, J + 1) of a row inside a group
+// (the CTA-pair kernel's wide units); a row's odd last tile gets a null
+// partner (I = J = 511: rows past any N, nothing is stored for it).
 void build_tiles(int N, int B, int tile, int halves, std::vector<uint32_t>& out, int& per_instance) {
   const int T = (N + tile - 1) / tile;
   const int G = g.tile_group;
@@ -181,7 +186,14 @@ void build_tiles(int N, int B, int tile, int halves, std::vector<uint32_t>& out,
     for (int gj = gi; gj < T; gj += G)
       for (int I = gi; I < std::min(gi + G, T); ++I)
         for (int J = std::max(I, gj); J < std::min(gj + G, T); ++J) {
-          if (halves) {
+          if (halves == 3) {
+            const bool pair = J + 1 < std::min(gj + G, T);
+            one.push_back(pack_tile(0, I, J, 0));
+            one.push_back(pack_tile(0, I, J, 1));
+            one.push_back(pair ? pack_tile(0, I, J + 1, 0) : pack_tile(0, 511, 511, 0));
+            one.push_back(pair ? pack_tile(0, I, J + 1, 1) : pack_tile(0, 511, 511, 1));
+            if (pair) ++J;
+          } else if (halves) {
             one.push_back(pack_tile(0, I, J, 0));
             if (halves == 2 || I * tile + tile / 2 < N) one.push_back(pack_tile(0, I, J, 1));
           } else {
@@ -198,7 +210,8 @@ void build_tiles(int N, int B, int tile, int halves, std::vector<uint32_t>& out,
 bool tc_precision(int p) { return p == SP2_PREC_SPLIT_FP16 || p == SP2_PREC_FP16; }
 
 // Uploads a uniform-size tile list (B instances of size N); kind 0 = FFMA
-// tiles, 1 = tensor-core halves, 2 = tensor-core super-tile pairs.
+// tiles, 1 = tensor-core halves, 2 = tensor-core super-tile pairs, 3 = the
+// pairs' wide units.
 sp2_status upload_tiles(int N, int B, int kind, int* ntiles_out) {
   std::vector<uint32_t> tiles;
   int per = 0;
@@ -462,6 +475,8 @@ sp2_status sp2_init(const sp2_config* cfg) {
     g.wave_sync = wsy ? std::max(0, std::min(4096, atoi(wsy))) : 16;
     const char* sn = getenv("SP2_SNAKE");
     g.snake = (sn && strcmp(sn, "1") == 0) ? 1 : 0;
+    const char* wd = getenv("SP2_WIDE");
+    g.wide = wd ? (strcmp(wd, "1") == 0 ? 1 : 0) : -1;
     const char* tg = getenv("SP2_TILE_GROUP");
     const int tgv = tg ? atoi(tg) : 8;
     if (tgv != g.tile_group) g.tiles_key_N = -1;
@@ -690,8 +705,22 @@ sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int
   const bool split = prec == SP2_PREC_SPLIT_FP16;
   cudaStream_t st = g.stream;
 
+  // CTA pairs on wide units (two super tiles of a row per pass, a quarter
+  // fewer operand bytes) where that takes no more waves of 76 pairs, counted
+  // in super-tile times, than single super tiles (SP2_WIDE=0/1 forces it)
+  bool wide = false;
+  if (tc && g.pair_kernel && g.wide != 0) {
+    const int T = (N + kTcBN - 1) / kTcBN, npairs = std::max(1, g.num_sms / 2);
+    const int nsup = T * (T + 1) / 2;
+    std::vector<uint32_t> wl;
+    int per = 0;
+    build_tiles(N, 1, kTcBN, 3, wl, per);
+    const int nunits = per / 4;
+    const int waves = (nsup + npairs - 1) / npairs, waves_w = 2 * ((nunits + npairs - 1) / npairs);
+    wide = g.wide == 1 || (N >= 8192 && waves_w <= waves);
+  }
   int ntiles = 0;
-  CKS(upload_tiles(N, 1, tc ? (g.pair_kernel ? 2 : 1) : 0, &ntiles));
+  CKS(upload_tiles(N, 1, tc ? (g.pair_kernel ? (wide ? 3 : 2) : 1) : 0, &ntiles));
   void *ctl, *ns, *hs, *dptr, *err, *part, *tick;
   CKS(ws(B_CTL, sizeof(Ctl), &ctl));
   CKS(ws(B_NS, sizeof(int), &ns));
@@ -801,8 +830,10 @@ sp2_status density_matrix_impl(const float* H, int N, int N_occ, double tol, int
     // epoch counters of the soft pair synchronisation, one zeroed slice per launch
     unsigned* wave = nullptr;
     size_t wave_per_launch = 0;
+    A.wide = wide ? 1 : 0;
     if (g.pair_kernel && g.wave_sync > 0) {
       const int ncl = grid / 2, nsuper = ntiles / 2;
+      // units of work per pair: super tiles, or wide units of two
       const long long stages = (long long)((nsuper + ncl - 1) / ncl) * ((N + 63) / 64);
       wave_per_launch = (size_t)(stages / g.wave_sync + 2);
       void* wv;

@@ -603,11 +603,34 @@ __device__ __forceinline__ int tile(const SqArgs& a, int t, uint32_t it, uint32_
   return 1;
 }
 
+// The finisher warp's work for one active tile: waits for the tile's entry
+// (the it-th of the CTA), writes its per-tile sums and runs
+// finish_tile_warp (the instance's control step after its last tile).
+// False on an abort.
+__device__ __forceinline__ bool finish_entry(const SqArgs& a, uint32_t it, Shared& sh, volatile int* abort_flag,
+                                             int lane, unsigned long long lim) {
+  using namespace sp2::tc;
+  const uint32_t e = it % FQ;
+  if (!__all_sync(0xffffffffu, mbar_wait(&sh.fin_full[e], (it / FQ) & 1u, abort_flag, lim))) {
+    if (lane == 0) atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
+    *abort_flag = 1;
+    return false;
+  }
+  const FinEntry f = sh.fq[e];
+  if (lane == 0 && f.dots) {
+    a.tile_dots[3 * (long long)f.t + 0] = f.d0;
+    a.tile_dots[3 * (long long)f.t + 1] = f.d1;
+    a.tile_dots[3 * (long long)f.t + 2] = f.d2;
+  }
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&sh.fin_empty[e]);
+  finish_tile_warp(a, f.t, f.b, f.T, f.Q, f.out_mode);
+  return true;
+}
+
 // The finisher warp: for every active tile of the CTA, in the order the
 // epilogue warps take them (tile(t) for t = first, first + stride, ...),
-// waits for the tile's entry, writes its per-tile sums and runs
-// finish_tile_warp (the instance's control step after its last tile).
-// Returns early on an abort.
+// finish_entry.  Returns early on an abort.
 __device__ __forceinline__ void finisher(const SqArgs& a, int first, int stride, int count, Shared& sh,
                                          volatile int* abort_flag, int lane) {
   using namespace sp2::tc;
@@ -617,22 +640,28 @@ __device__ __forceinline__ void finisher(const SqArgs& a, int first, int stride,
     int b, I, J, h;
     unpack_tile(a.tiles[t], b, I, J, h);
     if (!load_params(a, b).active) continue;
-    const uint32_t e = it % FQ;
-    if (!__all_sync(0xffffffffu, mbar_wait(&sh.fin_full[e], (it / FQ) & 1u, abort_flag, lim))) {
-      if (lane == 0) atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
-      *abort_flag = 1;
-      return;
-    }
-    const FinEntry f = sh.fq[e];
-    if (lane == 0 && f.dots) {
-      a.tile_dots[3 * (long long)f.t + 0] = f.d0;
-      a.tile_dots[3 * (long long)f.t + 1] = f.d1;
-      a.tile_dots[3 * (long long)f.t + 2] = f.d2;
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&sh.fin_empty[e]);
-    finish_tile_warp(a, f.t, f.b, f.T, f.Q, f.out_mode);
+    if (!finish_entry(a, it, sh, abort_flag, lane, lim)) return;
     ++it;
+  }
+}
+
+// The finisher warp of a CTA-pair kernel: the CTA's tiles are
+// 2 (uw u + k) + rank for its units u = cl, cl + ncl, ... < nunits and
+// k < uw (uw super tiles per unit), in the epilogue warps' order.
+__device__ __forceinline__ void finisher_pair(const SqArgs& a, int cl, int ncl, int nunits, int uw, int rank,
+                                              Shared& sh, volatile int* abort_flag, int lane) {
+  using namespace sp2::tc;
+  const unsigned long long lim = wait_limit(a);
+  uint32_t it = 0;
+  for (int u = cl; u < nunits; u += ncl) {
+    for (int k = 0; k < uw; ++k) {
+      const int t = 2 * (uw * u + k) + rank;
+      int b, I, J, h;
+      unpack_tile(a.tiles[t], b, I, J, h);
+      if (!load_params(a, b).active) continue;
+      if (!finish_entry(a, it, sh, abort_flag, lane, lim)) return;
+      ++it;
+    }
   }
 }
 

@@ -83,6 +83,9 @@ struct SqArgs {
   // is still in L2.  wave_ctr: zeroed counters of this launch; nullptr = off.
   unsigned* wave_ctr;
   int sync_stages;
+  int wide;                // CTA-pair kernel: 1 = units of two super tiles (I, J), (I, J + 1) of a
+                           //    row (tile list with four entries per unit; a unit without a second
+                           //    tile has a null second entry, rows past N), A loaded once per stage
   int snake;               // 1: a pair walks K backwards on its odd-numbered tiles, so that a
                            //    wave starts on the K slices the previous wave left in L2
 };

@@ -40,6 +40,12 @@
 //   warp 10     finisher: publishes each tile's sums, runs the control steps
 // Plain FP16 (split = false): hi hi only, 32 KB stages, 6 stages.
 //
+// Wide units (SqArgs::wide, the single solve at large N): a pair takes the
+// super tiles (I, J) and (I, J + 1) of a row together, one per accumulator,
+// and loads their common A half once per K stage: a quarter fewer operand
+// bytes per FLOP, at the price of an epilogue that no longer overlaps the
+// next unit's MMAs.
+//
 // Operand reads use only the upper super tiles of the planes: a 64-wide K
 // block left of the diagonal (super column k < I for the A rows of super row
 // I, k < J for B) is read from the stored block (k, I) or (k, J) transposed,
@@ -66,6 +72,17 @@ constexpr int STAGE_SPLIT = 4 * HALF_BYTES;  // 64 KB: hpA loA hpB loB
 constexpr int STAGE_PLAIN = 2 * HALF_BYTES;  // 32 KB: hiA hiB
 constexpr int STAGES_SPLIT = 3;
 constexpr int STAGES_PLAIN = 6;
+// Wide units (SqArgs::wide): a pair computes the super tiles (I, J) and
+// (I, J + 1) together, loading the A half once per K stage for both: a stage
+// holds A, B of J and B of J + 1 (96 KB split, two stages; 48 KB plain, four),
+// the same 192 KB as the three 64 KB stages of one super tile.  The two
+// accumulators are the two products of the unit, so the epilogue of a unit
+// no longer runs under the MMAs of the next; the operand bytes per FLOP fall
+// by a quarter.
+constexpr int STAGE_WSPLIT = 6 * HALF_BYTES;
+constexpr int STAGE_WPLAIN = 3 * HALF_BYTES;
+constexpr int STAGES_WSPLIT = 2;
+constexpr int STAGES_WPLAIN = 4;
 constexpr int EPI_WARPS = epi::WARPS;
 constexpr int FIN_WARP = 2 + EPI_WARPS;  // the finisher warp (after the epilogue warps)
 constexpr int THREADS = 64 + 32 * EPI_WARPS + 32;
@@ -89,6 +106,8 @@ __device__ __forceinline__ int pair_n(int N, int J) { return N - J * BN <= BH ? 
 constexpr int T_BOX = 64 * 64 * 2;
 // stage offsets (split): hpA, loA, hpB, loB
 constexpr int OFF_HPA = 0, OFF_LOA = HALF_BYTES, OFF_HPB = 2 * HALF_BYTES, OFF_LOB = 3 * HALF_BYTES;
+// wide units: the second B half (J + 1) after the first (split: hp, lo'; plain: hi)
+constexpr int OFF_HPB1 = 4 * HALF_BYTES, OFF_LOB1 = 5 * HALF_BYTES, OFF_B1_PLAIN = 2 * HALF_BYTES;
 
 // Loads one 128-row operand half of K block k0 into dst: K-major (one box of
 // 64 x 128) when the block lies on or right of the diagonal, else the stored
@@ -135,7 +154,7 @@ __device__ __forceinline__ bool epoch_wait(const unsigned* ctr, unsigned need, u
 // boxes for the B half; tm_p0T / tm_p1T: 64 x 64 boxes (transposed reads).
 // The kernel body; the map arguments point at the kernels' __grid_constant__
 // parameters (for one segment the second set repeats the first).
-template <bool SPLIT, bool RO, bool NSEG2>
+template <bool SPLIT, bool RO, bool NSEG2, bool WIDE>
 __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const CUtensorMap& tm_p1A,
                                               const CUtensorMap& tm_p0B, const CUtensorMap& tm_p1B,
                                               const CUtensorMap& tm_p0T, const CUtensorMap& tm_p1T,
@@ -143,8 +162,10 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
                                               const CUtensorMap& tm2_p0B, const CUtensorMap& tm2_p1B,
                                               const CUtensorMap& tm2_p0T, const CUtensorMap& tm2_p1T,
                                               const SqArgs& a) {
-  constexpr int STAGES = SPLIT ? STAGES_SPLIT : STAGES_PLAIN;
-  constexpr int STAGE_BYTES = SPLIT ? STAGE_SPLIT : STAGE_PLAIN;
+  constexpr int STAGES = WIDE ? (SPLIT ? STAGES_WSPLIT : STAGES_WPLAIN) : (SPLIT ? STAGES_SPLIT : STAGES_PLAIN);
+  constexpr int STAGE_BYTES = WIDE ? (SPLIT ? STAGE_WSPLIT : STAGE_WPLAIN) : (SPLIT ? STAGE_SPLIT : STAGE_PLAIN);
+  constexpr int UW = WIDE ? 2 : 1;  // super tiles per unit of work of a pair
+  static_assert(!WIDE || (!RO && !NSEG2), "wide units serve the single solve");
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -172,14 +193,14 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
   // an instance can finish within this launch only after all of its tiles,
   // these among them, have been processed.
   if (warp == 0) {
-    const int c0 = (int)(blockIdx.x >> 1), nc = (int)(gridDim.x >> 1), ns = a.ntiles >> 1;
+    const int c0 = (int)(blockIdx.x >> 1), nc = (int)(gridDim.x >> 1), ns = (a.ntiles >> 1) / UW;
     bool any = false;
     for (int u0 = c0; u0 < ns && !any; u0 += 32 * nc) {
       const int u = u0 + lane * nc;
       bool act = false;
       if (u < ns) {
         int b, I, J, h;
-        unpack_tile(a.tiles[2 * u], b, I, J, h);
+        unpack_tile(a.tiles[2 * UW * u], b, I, J, h);
         act = load_params(a, b).active != 0;
       }
       any = __any_sync(0xffffffffu, act);
@@ -220,6 +241,7 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
   const uint32_t peer_abort = mapa_u32(smem_u32(&s_abort), peer);
   const int cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
   const int nsuper = a.ntiles >> 1;
+  const int nunits = nsuper / UW;  // a pair takes units cl, cl + ncl, ...
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -237,13 +259,22 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
       bool wait_sync = rank == 0 && a.wave_ctr != nullptr && W > 0;
       const bool pub_sync = wait_sync;
       uint32_t gs = 0;
-      for (int u = cl; u < nsuper && ok; u += ncl) {
+      for (int u = cl; u < nunits && ok; u += ncl) {
         int b, I, J, h;
-        unpack_tile(a.tiles[2 * u + (int)rank], b, I, J, h);
+        unpack_tile(a.tiles[2 * UW * u + (int)rank], b, I, J, h);
         if (!load_params(a, b).active) continue;
         const int N = a.Ns[b];
         // each CTA supplies half of the MMA's N rows of B
         const int rowA = I * BN + (int)rank * BH, rowB = J * BN + (int)rank * (pair_n(N, J) >> 1);
+        // wide units: the second super tile (I, J1), or none (a row's odd last tile)
+        int J1 = 0, rowB1 = 0;
+        bool two = false;
+        if (WIDE) {
+          int b1, I1, h1;
+          unpack_tile(a.tiles[2 * UW * u + 2 + (int)rank], b1, I1, J1, h1);
+          two = I1 * BN < N;
+          rowB1 = J1 * BN + (int)rank * (pair_n(N, J1) >> 1);
+        }
         const int nk = (N + BK - 1) / BK;
         const int nkt = NSEG2 ? 2 * nk : nk;  // K stages of the tile over both segments
         const bool rev = a.snake && (((u - cl) / ncl) & 1);
@@ -255,7 +286,7 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
             const uint32_t e = gs / (uint32_t)W - 1u;  // the epoch this pair just finished
             atomicAdd(&a.wave_ctr[e], 1u);
             if (wait_sync && e >= 1u)
-              wait_sync = epoch_wait(a.wave_ctr + (e - 1u), pairs_in_epoch(e - 1u, W, nkt, nsuper, ncl), lim);
+              wait_sync = epoch_wait(a.wave_ctr + (e - 1u), pairs_in_epoch(e - 1u, W, nkt, nunits, ncl), lim);
           }
           if (!mbar_wait_cl(&empty[stage], phase ^ 1u, abort_flag, lim)) {
             ok = false;
@@ -263,7 +294,9 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
           }
           uint8_t* st = smem + stage * STAGE_BYTES;
           if (rank == 0) {
-            mbar_expect_tx(&full[stage], 2 * STAGE_BYTES);
+            // a wide unit without its second tile loads no second B half
+            const int bytes = (WIDE && !two) ? STAGE_BYTES - (SPLIT ? 2 : 1) * HALF_BYTES : STAGE_BYTES;
+            mbar_expect_tx(&full[stage], 2 * bytes);
             ++armed[stage];
           }
           const uint32_t bar = full_cl + 8u * (uint32_t)stage;
@@ -284,9 +317,14 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
             load_half(st + OFF_LOA, mA1, mAT1, ks < I, rowA, k0, b, bar);
             load_half(st + OFF_HPB, mB0, mBT0, ks < J, rowB, k0, b, bar);
             load_half(st + OFF_LOB, mB1, mBT1, ks < J, rowB, k0, b, bar);
+            if (WIDE && two) {
+              load_half(st + OFF_HPB1, mB0, mBT0, ks < J1, rowB1, k0, b, bar);
+              load_half(st + OFF_LOB1, mB1, mBT1, ks < J1, rowB1, k0, b, bar);
+            }
           } else {
             load_half(st, mA0, mAT0, ks < I, rowA, k0, b, bar);
             load_half(st + HALF_BYTES, mB0, mBT0, ks < J, rowB, k0, b, bar);
+            if (WIDE && two) load_half(st + OFF_B1_PLAIN, mB0, mBT0, ks < J1, rowB1, k0, b, bar);
           }
           if (++stage == STAGES) {
             stage = 0;
@@ -328,24 +366,36 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
       bool ok = true, issued = false;
       // injected fault (SqArgs::stall): a wait that runs out after lim
       if (a.stall && !mbar_wait(never, 0, abort_flag, lim)) ok = false;
-      for (int u = cl; u < nsuper && ok; u += ncl) {
+      for (int u = cl; u < nunits && ok; u += ncl) {
         int b, I, J, h;
-        unpack_tile(a.tiles[2 * u], b, I, J, h);
+        unpack_tile(a.tiles[2 * UW * u], b, I, J, h);
         if (!load_params(a, b).active) continue;
         const int N = a.Ns[b];
         const int nk = (N + BK - 1) / BK;
         const int nkt = NSEG2 ? 2 * nk : nk;
         const bool rev = a.snake && (((u - cl) / ncl) & 1);
-        const uint32_t buf = it & 1u;
+        // wide units: the second super tile (I, J1) into the other accumulator
+        int J1 = 0;
+        bool two = false;
+        if (WIDE) {
+          int b1, I1, h1;
+          unpack_tile(a.tiles[2 * UW * u + 2], b1, I1, J1, h1);
+          two = I1 * BN < N;
+        }
+        const uint32_t buf = it & 1u;  // wide units: it is even, both buffers are used
         const uint32_t idesc_n = pair_n(N, J) == BH ? IDESC2_N128 : IDESC2;
+        const uint32_t idesc_n1 = pair_n(N, J1) == BH ? IDESC2_N128 : IDESC2;
         (void)h;
         // the k-th use of a buffer waits for the epilogues' (k-1)-th release
-        if (!mbar_wait_cl(&tmem_empty[buf], ((it >> 1) & 1u) ^ 1u, abort_flag, lim)) {
+        bool got = mbar_wait_cl(&tmem_empty[buf], ((it >> 1) & 1u) ^ 1u, abort_flag, lim);
+        if (WIDE && got) got = mbar_wait_cl(&tmem_empty[1], ((it >> 1) & 1u) ^ 1u, abort_flag, lim);
+        if (!got) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t d = tmem_base + buf * BN;
+        const uint32_t d1 = tmem_base + BN;  // wide units: the second accumulator
         for (int kk = 0; kk < nkt; ++kk) {
           const int kbt = rev ? nkt - 1 - kk : kk;
           const int kb = (NSEG2 && kbt >= nk) ? kbt - nk : kbt;  // K block within its segment
@@ -359,11 +409,14 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
           const int sc = kb * BK / BN;
           const bool ta = sc < I, tb = sc < J;
           const uint32_t idesc = idesc_n | (ta ? IDESC_A_MN : 0u) | (tb ? IDESC_B_MN : 0u);
+          const bool tb1 = sc < J1;
+          const uint32_t idesc1 = idesc_n1 | (ta ? IDESC_A_MN : 0u) | (tb1 ? IDESC_B_MN : 0u);
 #pragma unroll
           for (int ks = 0; ks < BK / UMMA_K; ++ks) {
             // K step ks: 32 B along a K-major row, or two 8-row K groups
             const uint32_t oa = ta ? ks * 2048u : ks * UMMA_K * 2u;
             const uint32_t ob = tb ? ks * 2048u : ks * UMMA_K * 2u;
+            const uint32_t ob1 = tb1 ? ks * 2048u : ks * UMMA_K * 2u;
             const uint32_t acc = (kk > 0 || ks > 0) ? 1u : 0u;
             if (SPLIT) {
               const uint64_t dhpA = ta ? make_desc_mn128(st + OFF_HPA + oa) : make_desc_sw128(st + OFF_HPA + oa);
@@ -373,10 +426,24 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
               mma_f16_pair(d, dhpA, dhpB, idesc, acc);  // hp hp
               mma_f16_pair(d, dloA, dhpB, idesc, 1u);   // lo' hp
               mma_f16_pair(d, dhpA, dloB, idesc, 1u);   // hp lo'
+              if (WIDE && two) {
+                const uint64_t dhpB1 =
+                    tb1 ? make_desc_mn128(st + OFF_HPB1 + ob1) : make_desc_sw128(st + OFF_HPB1 + ob1);
+                const uint64_t dloB1 =
+                    tb1 ? make_desc_mn128(st + OFF_LOB1 + ob1) : make_desc_sw128(st + OFF_LOB1 + ob1);
+                mma_f16_pair(d1, dhpA, dhpB1, idesc1, acc);
+                mma_f16_pair(d1, dloA, dhpB1, idesc1, 1u);
+                mma_f16_pair(d1, dhpA, dloB1, idesc1, 1u);
+              }
             } else {
               const uint64_t dA = ta ? make_desc_mn128(st + oa) : make_desc_sw128(st + oa);
               const uint64_t dB = tb ? make_desc_mn128(st + HALF_BYTES + ob) : make_desc_sw128(st + HALF_BYTES + ob);
               mma_f16_pair(d, dA, dB, idesc, acc);
+              if (WIDE && two) {
+                const uint64_t dB1 = tb1 ? make_desc_mn128(st + OFF_B1_PLAIN + ob1)
+                                         : make_desc_sw128(st + OFF_B1_PLAIN + ob1);
+                mma_f16_pair(d1, dA, dB1, idesc1, acc);
+              }
             }
           }
           // release the stage in both CTAs
@@ -391,7 +458,12 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
         if (!ok) break;
         mma_commit_pair(tfull_own + 8u * buf);
         mma_commit_pair(tfull_peer + 8u * buf);
-        ++it;
+        if (WIDE) {
+          // also when the unit has no second tile: its epilogue waits for it
+          mma_commit_pair(tfull_own + 8u);
+          mma_commit_pair(tfull_peer + 8u);
+        }
+        it += UW;
       }
       if (!ok || *abort_flag) {
         atomicExch(a.err, (int)SP2_ERR_DEVICE_TIMEOUT);
@@ -406,8 +478,8 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
     }
   } else if (warp == FIN_WARP) {
     // ------------------------------------------------------------ finisher
-    // (tiles t = 2 u + rank of u = cl, cl + ncl, ...)
-    epi::finisher(a, 2 * cl + (int)rank, 2 * ncl, 2 * nsuper, s_epi, abort_flag, lane);
+    // (tiles t = 2 (UW u + k) + rank of units u = cl, cl + ncl, ...)
+    epi::finisher_pair(a, cl, ncl, nunits, UW, (int)rank, s_epi, abort_flag, lane);
     if (*abort_flag && lane == 0) st_cluster_u32(peer_abort, 1u);
   } else {
     // ------------------------------------------------------------ epilogue
@@ -415,15 +487,21 @@ __device__ __forceinline__ void syrk_tc2_body(const CUtensorMap& tm_p0A, const C
     const int q = warp & 3;   // TMEM lane quarter
     const uint32_t empty_cl = mapa_u32(smem_u32(&tmem_empty[0]), 0);
     uint32_t it = 0;
-    for (int u = cl; u < nsuper; u += ncl) {
-      const int t = 2 * u + (int)rank;
-      const int rc = epi::tile<SPLIT, NSEG2, RO, true>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag, s_epi,
-                                                        ew, q, lane, trbuf + ew * epi::TR_FLOATS, empty_cl);
-      if (rc < 0) {
-        if (lane == 0) st_cluster_u32(peer_abort, 1u);
-        break;
+    bool ok = true;
+    for (int u = cl; u < nunits && ok; u += ncl) {
+      // a unit's super tiles use the accumulator buffers in turn (a wide
+      // unit's second tile, when it has none, has no rows to store)
+      for (int k = 0; k < UW; ++k) {
+        const int t = 2 * (UW * u + k) + (int)rank;
+        const int rc = epi::tile<SPLIT, NSEG2, RO, true>(a, t, it, tmem_base, tmem_full, tmem_empty, abort_flag,
+                                                          s_epi, ew, q, lane, trbuf + ew * epi::TR_FLOATS, empty_cl);
+        if (rc < 0) {
+          if (lane == 0) st_cluster_u32(peer_abort, 1u);
+          ok = false;
+          break;
+        }
+        it += (uint32_t)rc;
       }
-      it += (uint32_t)rc;
     }
   }
 
@@ -445,8 +523,19 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const __grid_constant__ CUtensorMap tm_p0B, const __grid_constant__ CUtensorMap tm_p1B,
                     const __grid_constant__ CUtensorMap tm_p0T, const __grid_constant__ CUtensorMap tm_p1T,
                     const SqArgs a) {
-  syrk_tc2_body<SPLIT, RO, false>(tm_p0A, tm_p1A, tm_p0B, tm_p1B, tm_p0T, tm_p1T, tm_p0A, tm_p1A, tm_p0B, tm_p1B,
-                                  tm_p0T, tm_p1T, a);
+  syrk_tc2_body<SPLIT, RO, false, false>(tm_p0A, tm_p1A, tm_p0B, tm_p1B, tm_p0T, tm_p1T, tm_p0A, tm_p1A, tm_p0B,
+                                         tm_p1B, tm_p0T, tm_p1T, a);
+}
+
+// Wide units (the single solve): super tiles (I, J) and (I, J + 1) per pass.
+template <bool SPLIT>
+__global__ void __launch_bounds__(THREADS, 1)
+    syrk_tc2_wide_kernel(const __grid_constant__ CUtensorMap tm_p0A, const __grid_constant__ CUtensorMap tm_p1A,
+                         const __grid_constant__ CUtensorMap tm_p0B, const __grid_constant__ CUtensorMap tm_p1B,
+                         const __grid_constant__ CUtensorMap tm_p0T, const __grid_constant__ CUtensorMap tm_p1T,
+                         const SqArgs a) {
+  syrk_tc2_body<SPLIT, false, false, true>(tm_p0A, tm_p1A, tm_p0B, tm_p1B, tm_p0T, tm_p1T, tm_p0A, tm_p1A, tm_p0B,
+                                           tm_p1B, tm_p0T, tm_p1T, a);
 }
 
 // Two K segments (the network adjoint's Y G + G Y): six maps per segment.
@@ -459,8 +548,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                          const __grid_constant__ CUtensorMap tm2_p0B, const __grid_constant__ CUtensorMap tm2_p1B,
                          const __grid_constant__ CUtensorMap tm2_p0T, const __grid_constant__ CUtensorMap tm2_p1T,
                          const SqArgs a) {
-  syrk_tc2_body<SPLIT, false, true>(tm_p0A, tm_p1A, tm_p0B, tm_p1B, tm_p0T, tm_p1T, tm2_p0A, tm2_p1A, tm2_p0B,
-                                    tm2_p1B, tm2_p0T, tm2_p1T, a);
+  syrk_tc2_body<SPLIT, false, true, false>(tm_p0A, tm_p1A, tm_p0B, tm_p1B, tm_p0T, tm_p1T, tm2_p0A, tm2_p1A, tm2_p0B,
+                                           tm2_p1B, tm2_p0T, tm2_p1T, a);
 }
 
 }  // namespace tc2
@@ -484,6 +573,9 @@ cudaError_t set_smem_once(K kernel, int bytes, int which) {
 size_t syrk_tc2_smem_bytes(bool split) {
   const int stages = split ? tc2::STAGES_SPLIT : tc2::STAGES_PLAIN;
   const int sb = split ? tc2::STAGE_SPLIT : tc2::STAGE_PLAIN;
+  static_assert(tc2::STAGES_WSPLIT * tc2::STAGE_WSPLIT == tc2::STAGES_SPLIT * tc2::STAGE_SPLIT &&
+                    tc2::STAGES_WPLAIN * tc2::STAGE_WPLAIN == tc2::STAGES_PLAIN * tc2::STAGE_PLAIN,
+                "wide units use the same shared memory as single super tiles");
   return (size_t)stages * sb + 1024 /* alignment slack */ + 256 /* barriers */ + epi::TR_BYTES;
 }
 
@@ -516,6 +608,8 @@ cudaError_t launch_syrk_tc2(const SqArgs& a, const CUtensorMap* tm, bool split, 
   cudaError_t e;
   if (a.nseg == 2)
     e = split ? go2(tc2::syrk_tc2_seg2_kernel<true>, 5) : go2(tc2::syrk_tc2_seg2_kernel<false>, 4);
+  else if (a.wide)
+    e = split ? go(tc2::syrk_tc2_wide_kernel<true>, 7) : go(tc2::syrk_tc2_wide_kernel<false>, 6);
   else if (a.R)
     e = split ? go(tc2::syrk_tc2_kernel<true, true>, 3) : go(tc2::syrk_tc2_kernel<false, true>, 2);
   else

@@ -71,3 +71,39 @@ def test_n16384_whole_super_rows(big):
         print(f"super row {I}: max_abs over {got.size} entries = {err:.3e}")
         assert err <= 5e-5
     print(f"N={N}: whole super rows worst max_abs = {worst:.3e}")
+
+
+@pytest.mark.parametrize("N", [1000, 4096])
+def test_wide_units_match_single_super_tiles(N):
+    """The CTA-pair kernel's wide units (two super tiles of a row per pass,
+    the A panel loaded once; chosen automatically at N = 16384) give the same
+    bits as one super tile per pass: each tile's products and epilogue are
+    unchanged, only the order of the FP64 tile partials differs, and no
+    branch decision moves.  Both sizes have rows with an odd last tile (a
+    unit with a null second tile)."""
+    import os
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2101_06385_gb300 as sp2
+
+    h = si.gapped_hamiltonian(N, N // 2, (-1.0, -0.05), (0.05, 1.0), seed=60 + N % 89)
+    H = torch.from_numpy(h.h32()).cuda()
+    out = {}
+    try:
+        for mode in ("0", "1"):
+            os.environ["SP2_WIDE"] = mode
+            sp2.finalize()
+            sp2.init(0)
+            D, st = sp2.density_matrix(H, N // 2, precision="split")
+            assert st.status == 0, st
+            out[mode] = (D.clone(), st.iterations, st.sigmas)
+    finally:
+        os.environ.pop("SP2_WIDE", None)
+        sp2.finalize()
+        sp2.init(0)
+    assert torch.equal(out["0"][0], out["1"][0])
+    assert out["0"][1:] == out["1"][1:]
+    m = o.error_metrics(out["1"][0].cpu().numpy().astype(np.float64), o.density_matrix_closed_form(h.Q, N // 2),
+                        N // 2)
+    assert m["max_abs"] <= 5e-5 and m["trace_err"] <= 1e-4, m
