@@ -675,7 +675,7 @@ def run_ours(args):
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{src} bf16_tflops_sustained (FP16 dense = BF16 dense rate)",
-                     "kernel": "syrk_tc2_kernel<split> (CTA pairs)", "launch_ms_mean": launch_ms,
+                     "kernel": "syrk_tc2_kernel<split> (CTA pairs; wide units at N = 16384)", "launch_ms_mean": launch_ms,
                      "idle_launch_ms_mean": statistics.mean(idle) if idle else None,
                      "executed_tflops": exec_flops / (launch_ms * 1e-3) / 1e12},
         "accelerated": accel,
