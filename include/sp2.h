@@ -115,7 +115,18 @@ typedef struct {
 
 /* Library set-up.  cfg == NULL selects the defaults {device 0, NULL stream,
  * SPLIT_FP16, s = 11, shift on, eps 0}.  Calling again re-applies a config
- * (the workspace is kept).  Errors: INVALID_ARG (bad field), CUDA. */
+ * (the workspace is kept).  Errors: INVALID_ARG (bad field), CUDA.
+ * Schedule switches read here from the environment (none changes a result
+ * except where stated): SP2_SQUARE_KERNEL=single (single CTAs instead of CTA
+ * pairs), SP2_BATCHED_KERNEL=single|pairs (fix the batched schedule instead
+ * of timing both on the first call of a batch signature), SP2_GRAPHS=0
+ * (enqueue the batched launches directly instead of replaying a CUDA graph),
+ * SP2_WAVE_SYNC=<K stages> (epoch of the pairs' soft synchronisation in the
+ * single solve, 16; 0 off), SP2_TILE_GROUP=<n> (side of the square tile
+ * groups, 8), SP2_WIDE=0|1 (two super tiles of a row per pair pass in the
+ * single solve; default: where it takes no more waves, i.e. N = 16384),
+ * SP2_SNAKE=1 (alternate waves walk K backwards: changes the accumulation
+ * order), SP2_FAULT=<spec> (test-only fault injection, sp2_set_fault). */
 sp2_status sp2_init(const sp2_config* cfg);
 
 /* Frees the workspace.  Safe to call when not initialised. */

@@ -73,8 +73,8 @@ def test_n16384_whole_super_rows(big):
     print(f"N={N}: whole super rows worst max_abs = {worst:.3e}")
 
 
-@pytest.mark.parametrize("N", [1000, 4096])
-def test_wide_units_match_single_super_tiles(N):
+@pytest.mark.parametrize("N,precision", [(1000, "split"), (4096, "split"), (1000, "fp16"), (2053, "fp16")])
+def test_wide_units_match_single_super_tiles(N, precision):
     """The CTA-pair kernel's wide units (two super tiles of a row per pass,
     the A panel loaded once; chosen automatically at N = 16384) give the same
     bits as one super tile per pass: each tile's products and epilogue are
@@ -95,7 +95,7 @@ def test_wide_units_match_single_super_tiles(N):
             os.environ["SP2_WIDE"] = mode
             sp2.finalize()
             sp2.init(0)
-            D, st = sp2.density_matrix(H, N // 2, precision="split")
+            D, st = sp2.density_matrix(H, N // 2, precision=precision)
             assert st.status == 0, st
             out[mode] = (D.clone(), st.iterations, st.sigmas)
     finally:
@@ -106,4 +106,5 @@ def test_wide_units_match_single_super_tiles(N):
     assert out["0"][1:] == out["1"][1:]
     m = o.error_metrics(out["1"][0].cpu().numpy().astype(np.float64), o.density_matrix_closed_form(h.Q, N // 2),
                         N // 2)
-    assert m["max_abs"] <= 5e-5 and m["trace_err"] <= 1e-4, m
+    tol = 5e-5 if precision == "split" else 2e-3
+    assert m["max_abs"] <= tol and m["trace_err"] <= 1e-4 * (1 if precision == "split" else 20), m
