@@ -163,7 +163,7 @@ class Clocks:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], None, set()
+        sm, smax, reasons, pw = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
             for line in f:
@@ -175,12 +175,17 @@ class Clocks:
                     smax = float(parts[2])
                 except ValueError:
                     continue
+                try:
+                    pw.append(float(parts[3]))
+                except ValueError:
+                    pass
                 for nm, v in zip(names, parts[5:9]):
                     if v.lower().startswith("active"):
                         reasons.add(nm)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w": statistics.median(pw) if pw else None}
 
 
 # sources that define the timed squaring kernel; the committed DRAM-traffic
@@ -207,6 +212,15 @@ def _traffic_from_profile(n):
     if not m or not t:
         return None
     return float(t.group(1)) if kernel_source_hash() == m.group(1) else None
+
+
+def energy_of(power_w, ms_per_solve, layers):
+    """Energy of one solve and one squaring layer from the median board power
+    sampled during the timed region (None when no power was sampled)."""
+    if not power_w or not ms_per_solve or not layers:
+        return None
+    j = power_w * ms_per_solve * 1e-3
+    return {"power_w_median": power_w, "joules_per_solve": j, "joules_per_layer": j / layers}
 
 
 def _oracle_one_core(n=4096, rows=256):
@@ -684,6 +698,8 @@ def run_ours(args):
         "fermi_expansion": fermi,
         "cpu_baseline": cpu,
         "clocks": clocks,
+        # board power sampled during the timed solves and the energy it implies
+        "energy": energy_of(clocks.get("power_w"), ms, layers),
         "gpu_launches": int(launches_per_step * args.steps),
     }
     if rank == 0:

@@ -36,3 +36,14 @@ def test_layer_sample_checksum_is_the_rows_of_the_layer(rows):
     S = (A + A.T) / 2
     want = float(np.trace((2.0 * S - S @ S)[:rows, :rows]))
     assert abs(oracle.sp2_layer_sample(S, rows) - want) <= 1e-10 * max(1.0, abs(want))
+
+
+def test_energy_from_sampled_power():
+    """Energy of a solve = median sampled board power x time-to-D; per layer
+    divided by the squaring layers; nothing when no power was sampled."""
+    e = bench.energy_of(1400.0, 400.0, 50)
+    assert e["power_w_median"] == 1400.0
+    assert abs(e["joules_per_solve"] - 560.0) < 1e-9
+    assert abs(e["joules_per_layer"] - 11.2) < 1e-9
+    assert bench.energy_of(None, 400.0, 50) is None
+    assert bench.energy_of(1400.0, 400.0, 0) is None
